@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the densest-subgraph hot path on one GB300 (or N replicas).
+
+One step = the whole hot path over one synthetic graph:
+  ingest (raw pairs -> canonical CSR, on the device)
+  + the Bahmani peel (Algorithm 1) at every eps of the workload
+  + core numbers (Algorithm 2, first phase).
+Metric: adjacency entries scanned per second (each solve reads every row
+once: 2m entries per peel and per core decomposition), bit-exact outputs.
+
+Default workload: R-MAT scale 20 (2^20 vertices, 2^24 generated pairs,
+a=.57 b=.19 c=.19, seed 1), eps in {1/1000, 1/10, 1}.  Inputs are resident in
+HBM before the timed region; L2 is flushed (a 512 MiB write) before every
+timed step.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the same workload instead (the reference arm of this project).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+WORKLOADS = {
+    "rmat20": dict(
+        desc="R-MAT scale 20 (1,048,576 vertices, 16,777,216 generated pairs, a=.57 b=.19 c=.19, seed 1), "
+             "symmetrized, deduped, loops dropped; Bahmani eps in {1/1000, 1/10, 1} + core numbers",
+        gen=lambda: inputs.rmat(scale=20, m=1 << 24, a=0.57, b=0.19, c=0.19, seed=1),
+        eps=[(1, 1000), (1, 10), (1, 1)]),
+    "er1e4": dict(
+        desc="Erdos-Renyi G(n=10,000, m=50,000) seed 0 + planted 100-vertex block at p=0.5; "
+             "Bahmani eps=1/10 + core numbers",
+        gen=lambda: inputs.er_block(n=10_000, m=50_000, k=100, p=0.5, seed=0),
+        eps=[(1, 10)]),
+    "cl24": dict(
+        desc="Chung-Lu n=16,777,216, exponent 2.1, mean degree 32, max expected degree 100,000, seed 2, "
+             "2^28 generated pairs; Bahmani eps=1/10 + core numbers",
+        gen=lambda: inputs.chung_lu(n=1 << 24, m_draws=1 << 28, gamma=2.1, mean=32.0, wmax=1e5, seed=2),
+        eps=[(1, 10)]),
+}
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------- byte model (per launch)
+def peel_bytes(n: int, m: int, st: dict) -> int:
+    """Algorithmic bytes of one peel launch (alive-list schedule):
+    adjacency 8m; two offsets per failed vertex 16n; state mark write 4n;
+    per round the alive id + state read 8|S_r| (round 0 reads no id: 4n) and
+    the survivor list write 4|S_{r+1}|; per adjacency entry one state read
+    (4 B), plus a 4 B write for each decrement of an alive neighbour."""
+    sum_S = st["sum_S"]
+    sum_S1 = st["sum_S"] - n  # sum over r of |S_{r+1}| = sum_{r>=1} |S_r|
+    return (8 * m + 16 * n + 4 * n + 8 * sum_S - 4 * n + 4 * sum_S1 + 4 * 2 * m + 4 * st["decrements"])
+
+
+def kcore_bytes(n: int, m: int, st: dict) -> int:
+    """Algorithmic bytes of one core-number launch: adjacency 8m; offsets of
+    every frontier vertex 16n; degree init write 4n; per level the remaining
+    id + degree read 8|R_k| (level 0 reads no id); per adjacency entry one
+    degree read 4 B; each atomic (decrement or undo) 4 B write; remaining-list
+    writes 4 B each."""
+    return (8 * m + 16 * n + 4 * n + 8 * st["rem_scanned"] - 4 * n + 4 * 2 * m + 4 * st["atomics"]
+            + 4 * st["rem_written"])
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, wl, raw, rank, world):
+    import torch
+    import paper_2103_00154_gb300 as dsg
+    from paper_2103_00154_gb300 import _native as N
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    L = dsg.lib()
+    stream = torch.cuda.current_stream()
+    n = raw.n
+    src_d = torch.from_numpy(raw.src.view(np.int32)).to(dev)
+    dst_d = torch.from_numpy(raw.dst.view(np.int32)).to(dev)
+    masks = [torch.empty(n, dtype=torch.uint8, device=dev) for _ in wl["eps"]]
+    core_d = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    results = {}
+
+    def step():
+        g = dsg.Graph.from_edges(n, src_d, dst_d, stream=stream)
+        for i, (p, q) in enumerate(wl["eps"]):
+            _, E, V = g.bahmani(p, q, out_set=masks[i])
+            results[(p, q)] = (E, V)
+        g.kcore(out=core_d)
+        m = g.m
+        g.close()
+        return m
+
+    for _ in range(max(args.warmup, 0)):
+        m = step()
+    torch.cuda.synchronize()
+
+    # counters for the byte model, from one traced solve of each kind (outside the timed region)
+    g = dsg.Graph.from_edges(n, src_d, dst_d, stream=stream)
+    m = g.m
+    peel_stats = []
+    for (p, q) in wl["eps"]:
+        tr = g.bahmani_trace(p, q)
+        peel_stats.append({"sum_S": int(tr.hist_S[:-1].sum()), "decrements": int(tr.decrements),
+                           "rounds": tr.rounds})
+    _, kst = g.kcore_counters()
+    g.close()
+
+    events = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    L.dsg_profile_reset()
+    L.dsg_profile_enable(1)
+    launches0 = L.dsg_launch_count()
+    with ClockSampler(dev.index) as clk:
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            events.append((a, b))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    launches = L.dsg_launch_count() - launches0
+    L.dsg_profile_enable(0)
+    prof = N.profile_report()
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    edges_per_step = 2 * m * (len(wl["eps"]) + 1)
+    value = edges_per_step * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (largest share of timed device time)
+    peak, peak_kind = measured_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if top:
+        name, (cnt, ms) = top
+        if name == "peel_rounds":
+            per_launch = [peel_bytes(n, m, s) for s in peel_stats]
+            alg = sum(per_launch) / len(per_launch)
+        elif name == "kcore_levels":
+            alg = kcore_bytes(n, m, kst)
+        else:
+            alg = None
+        if alg is not None:
+            avg_s = ms / cnt / 1e3
+            achieved = alg / avg_s / 1e9
+            roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "traffic": None, "alg_bytes_per_launch": int(alg), "avg_launch_ms": round(ms / cnt, 4)}
+    shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()} if prof else {}
+    out = {
+        "ms_per_step": total_ms / args.steps,
+        "value": value,
+        "m": m,
+        "edges_per_step": edges_per_step,
+        "results": {f"{p}/{q}": list(v) for (p, q), v in results.items()},
+        "roofline": roof,
+        "kernel_share": shares,
+        "kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "wall_s": t_wall,
+        "peel_rounds": [s["rounds"] for s in peel_stats],
+        "kcore": kst,
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, wl, raw, dev, edges_per_step, world)
+    return out
+
+
+def run_e2e(args, wl, raw, dev, edges_per_step, world):
+    """Same metric through the public API with HOST buffers: the raw pairs are
+    copied from pinned memory inside the call, results read back to pinned
+    host buffers, every step."""
+    import torch
+    import paper_2103_00154_gb300 as dsg
+    n = raw.n
+    src_h = torch.from_numpy(raw.src.view(np.int32)).pin_memory()
+    dst_h = torch.from_numpy(raw.dst.view(np.int32)).pin_memory()
+    masks = [torch.empty(n, dtype=torch.uint8).pin_memory() for _ in wl["eps"]]
+    core_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g = dsg.Graph.from_edges(n, src_h, dst_h, stream=stream)
+        for i, (p, q) in enumerate(wl["eps"]):
+            g.bahmani(p, q, out_set=masks[i])
+        g.kcore(out=core_h)
+        g.close()
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = 8 * raw.m_raw
+    d2h = n * len(wl["eps"]) + 4 * n + 16 * len(wl["eps"])
+    return {"value": edges_per_step * steps * world / dt, "unit": "edges/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt / steps * 1e3}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_step(raw, eps):
+    import oracle
+    c = oracle.from_raw(raw)
+    for p, q in eps:
+        oracle.bahmani(c, p, q)
+    oracle.kcore_bz(c)
+    return c.m
+
+
+def run_cpu_baseline(wl, raw, seconds):
+    """The oracle as it stands, serial on one host core, on whole steps of
+    the same workload until about `seconds` of CPU time have passed."""
+    t0 = time.perf_counter()
+    steps = 0
+    m = 0
+    while True:
+        m = oracle_step(raw, wl["eps"])
+        steps += 1
+        if time.perf_counter() - t0 >= seconds or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    eps_step = 2 * m * (len(wl["eps"]) + 1)
+    return {"value": eps_step * steps / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} whole step(s) of the workload (ingest + {len(wl['eps'])} peel(s) + core numbers), "
+                      f"{dt:.1f} s, serial C oracle"}
+
+
+def run_reference(args, wl, raw):
+    import oracle
+    small = inputs.er_block(n=10_000, m=50_000, k=100, p=0.5, seed=0)
+    for _ in range(max(args.warmup, 0)):
+        oracle_step(small, wl["eps"])
+    t0 = time.perf_counter()
+    m = 0
+    for _ in range(args.steps):
+        m = oracle_step(raw, wl["eps"])
+    dt = time.perf_counter() - t0
+    eps_step = 2 * m * (len(wl["eps"]) + 1)
+    value = eps_step * args.steps / dt
+    return {"impl": "reference", "metric": "edges scanned/s", "value": value, "unit": "edges/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} whole step(s) of the workload, warm-up on the 1e4-vertex case"},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        raw = wl["gen"]()
+        print(json.dumps(run_reference(args, wl, raw)), flush=True)
+        return 0
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    raw = wl["gen"]()
+    res = run_ours(args, wl, raw, rank, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = run_cpu_baseline(wl, raw, args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": "edges scanned/s",
+            "value": res["value"],
+            "unit": "edges/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "n": raw.n, "m_raw": raw.m_raw,
+                       "m": res["m"], "edges_scanned_per_step": res["edges_per_step"],
+                       "l2": "flushed before every timed step (512 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "graphs_per_s": world * args.steps / (res["ms_per_step"] * args.steps / 1e3),
+            "roofline": res["roofline"],
+            "cpu_baseline": cpu,
+            "e2e": res.get("e2e"),
+            "gpu_launches": res["gpu_launches"],
+            "clocks": res["clocks"],
+            "kernel_share": res["kernel_share"],
+            "kernel_ms_per_step": res["kernel_ms"],
+            "peel_rounds": res["peel_rounds"],
+            "kcore_counters": res["kcore"],
+            "results": res["results"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

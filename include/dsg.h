@@ -1,0 +1,212 @@
+/*
+ * dsg.h -- C ABI of libdsg, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of "Parallel Algorithms for Densest Subgraph
+ * Discovery Using Shared Memory Model" (De Zoysa et al., arXiv 2103.00154):
+ *
+ *   - the round-synchronous (2+2eps) densest-subgraph peel of Algorithm 1
+ *     (P-Bahmani), with the threshold test done exactly in integers, and
+ *   - core numbers by the level-synchronous peel of Algorithm 2's first
+ *     phase (PKC).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a dsg_status.  On error the outputs are left
+ *     untouched and dsg_last_error() gives a message (thread-local).
+ *   - Graphs are simple and undirected with vertices 0..n-1 (Def. 1).
+ *     n must be below 2^31.  Adjacency is CSR: off[n+1] (uint64), adj[off[n]]
+ *     (uint32); each edge appears in both rows; rows sorted ascending, no
+ *     self-loops, no repeats ("canonical").
+ *   - Pointer arguments are host or device pointers; the library tells them
+ *     apart with cudaPointerGetAttributes.  Input arrays are copied unless
+ *     DSG_PTRS_DEVICE is given, in which case the caller keeps ownership and
+ *     the arrays must outlive the graph handle.  Output arrays are
+ *     caller-allocated (host or device memory).
+ *   - Each graph handle carries a CUDA stream (given at creation, the
+ *     legacy default stream if NULL); all work of calls on that handle is
+ *     ordered on it.  The calls below return once their results are
+ *     written (they synchronise that stream).
+ *   - Density values are exact rationals E/V (uint64 pairs).
+ */
+#ifndef DSG_H
+#define DSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DSG_OK = 0,
+    DSG_EINVAL = 1,     /* bad argument: null pointer, q == 0, n >= 2^31, malformed CSR under VALIDATE */
+    DSG_ENOMEM = 2,     /* device or host allocation failed */
+    DSG_ECUDA = 3,      /* a CUDA runtime call failed */
+    DSG_ETIMEOUT = 4,   /* a bounded device-side wait ran out (the kernel returned; the context stays usable) */
+    DSG_EBUSY = 5,      /* serving: no slot / memory free right now (back-pressure) */
+    DSG_EAGAIN = 6,     /* serving: result not ready yet */
+    DSG_ENOTFOUND = 7,  /* serving: unknown ticket */
+    DSG_EOVERFLOW = 8   /* an output capacity given by the caller is too small */
+} dsg_status;
+
+/* flags for dsg_graph_from_csr / dsg_graph_from_edges */
+#define DSG_CSR_CANONICALIZE 0x1u /* input may hold loops, repeats, one-sided edges, unsorted rows */
+#define DSG_CSR_VALIDATE 0x2u     /* check the CSR is canonical on the device; DSG_EINVAL if not */
+#define DSG_PTRS_DEVICE 0x4u      /* inputs are device pointers owned by the caller (no copy) */
+
+typedef struct dsg_graph dsg_graph; /* opaque: device CSR plus the stream of its calls */
+
+/* ---------------------------------------------------------------- graphs */
+
+/*
+ * Build a device graph from a CSR (Def. 1 graph; the paper's "super map" of
+ * Sec. 3.1 "Data structures" is replaced by CSR over ids 0..n-1).
+ *   n      vertex count (< 2^31)
+ *   off    n+1 uint64 row offsets, off[0] = 0
+ *   adj    off[n] uint32 neighbour ids
+ *   flags  DSG_CSR_CANONICALIZE | DSG_CSR_VALIDATE | DSG_PTRS_DEVICE
+ *          (CANONICALIZE runs the edge-list ingest on the CSR entries and
+ *          always copies; it cannot be combined with PTRS_DEVICE ownership)
+ *   stream cudaStream_t for this graph's work (NULL: default stream)
+ *   out    receives the handle (free with dsg_graph_free)
+ */
+dsg_status dsg_graph_from_csr(uint32_t n, const uint64_t* off, const uint32_t* adj, uint32_t flags, void* stream,
+                              dsg_graph** out);
+
+/*
+ * Ingest raw undirected pairs (src[i], dst[i]), i < m_raw, over ids 0..n-1:
+ * drop self-loops, merge repeats and both orientations, emit both
+ * directions, sort each row (Def. 1: E is a set of edges between distinct
+ * vertices).  Runs on the device.  With DSG_PTRS_DEVICE, src/dst are device
+ * arrays read in place.  DSG_EINVAL if an id is >= n.
+ */
+dsg_status dsg_graph_from_edges(uint32_t n, uint64_t m_raw, const uint32_t* src, const uint32_t* dst, uint32_t flags,
+                                void* stream, dsg_graph** out);
+
+/* n and the undirected edge count m (= off[n]/2) of a graph. */
+dsg_status dsg_graph_info(const dsg_graph* g, uint32_t* n, uint64_t* m);
+
+/* Copy the canonical CSR out: off[n+1], adj[2m] (host or device buffers). */
+dsg_status dsg_graph_csr(const dsg_graph* g, uint64_t* off, uint32_t* adj);
+
+/* Re-target the graph's calls to another stream. */
+dsg_status dsg_graph_set_stream(dsg_graph* g, void* stream);
+
+/* Release a graph and its device memory.  NULL is ignored. */
+void dsg_graph_free(dsg_graph* g);
+
+/* ----------------------------------------------------- Algorithm 1 (peel) */
+
+/*
+ * Bahmani (2+2eps) peel, Algorithm 1 (P-Bahmani), eps = eps_num/eps_den:
+ *   S_0 = V; in round r every v in S_r with deg_{S_r}(v) <= 2(1+eps)|E(S_r)|/|S_r|
+ *   fails (tested exactly: deg * q * |S| <= 2 (p+q) |E|, against the degrees
+ *   at the start of the round); failed vertices and their edges leave;
+ *   |S| and |E(S)| are reduced; the densest S seen is kept, strict ">" so the
+ *   earliest round wins a tie; the loop stops when S is empty.  eps = 0 is
+ *   allowed.
+ *   out_set  n bytes, nullable: 1 for vertices of the densest set found
+ *   out_E/V  nullable: |E(S~)| and |S~| (zero for n = 0)
+ * DSG_EINVAL if eps_den == 0.
+ */
+dsg_status dsg_bahmani(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, uint8_t* out_set, uint64_t* out_E,
+                       uint64_t* out_V);
+
+/* Full record of one peel (Algorithm 1), for checking and analysis. */
+typedef struct {
+    uint64_t rounds;      /* out: R, the number of rounds run */
+    uint64_t best_round;  /* out: round whose set S_r is the answer */
+    uint64_t best_E;      /* out: |E(S~)| */
+    uint64_t best_V;      /* out: |S~| */
+    uint64_t hist_cap;    /* in: capacity of hist_S / hist_E (needs R+1) */
+    uint64_t* hist_S;     /* out, nullable: |S_r| for r = 0..R */
+    uint64_t* hist_E;     /* out, nullable: |E(S_r)| for r = 0..R */
+    uint32_t* peel_round; /* out, nullable, n entries: round (1-based) in which v failed */
+    uint8_t* out_set;     /* out, nullable, n entries: membership in S~ */
+    uint64_t edges_scanned; /* out: adjacency entries read by the neighbour scans (= 2m) */
+    uint64_t decrements;    /* out: degree decrements of surviving neighbours (edges whose
+                               ends failed in different rounds) */
+} dsg_trace;
+
+/* As dsg_bahmani, recording the per-round history.  DSG_EOVERFLOW if
+ * hist_cap < R+1 (the scalar outputs are still written). */
+dsg_status dsg_bahmani_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, dsg_trace* t);
+
+/* Upper bound on R+1 for a graph of n vertices: ceil(log_{(p+q)/q} n) + 2
+ * when p > 0 (each round with edges leaves fewer than q/(p+q) of the
+ * vertices), n + 1 when p == 0. */
+uint64_t dsg_round_bound(uint32_t n, uint32_t eps_num, uint32_t eps_den);
+
+/* --------------------------------------------- Algorithm 2, first phase */
+
+/*
+ * Core numbers (Def. 2) by the level-synchronous peel of Algorithm 2's first
+ * phase (PKC): level k collects the remaining vertices of degree k, then
+ * drains them, taking one from each neighbour above k and collecting a
+ * neighbour when it reaches k; levels with no vertex are skipped.
+ *   out_core  n uint32 (host or device)
+ */
+dsg_status dsg_kcore(const dsg_graph* g, uint32_t* out_core);
+
+/* As dsg_kcore, also writing up to nstats counters of the run into stats:
+ *   [0] levels run (including skipped-to empty ones)
+ *   [1] drain sub-rounds (grid-wide steps)
+ *   [2] remaining-list entries scanned (sum over levels)
+ *   [3] remaining-list entries written (sum over levels)
+ *   [4] degree atomics issued (decrements plus undos) */
+dsg_status dsg_kcore_stats(const dsg_graph* g, uint32_t* out_core, uint64_t* stats, uint32_t nstats);
+
+/* ------------------------------------------------------------- tuning */
+
+/*
+ * Launch parameters of the round kernels (not part of the method):
+ *   block          threads per block of the persistent kernels: 256, 512, 1024
+ *   blocks_per_sm  resident blocks per SM (0 = as many as fit)
+ *   short_max      rows up to this length are scanned edge-balanced inside a
+ *                  block; longer rows are cut into chunk items
+ *   chunk_len      entries per chunk item (one warp each), >= 32
+ * Process-wide; also read from DSG_BLOCK, DSG_BLOCKS_PER_SM, DSG_SHORT_MAX and
+ * DSG_CHUNK_LEN at first use.  Results never depend on these.
+ */
+dsg_status dsg_set_tuning(uint32_t block, uint32_t blocks_per_sm, uint32_t short_max, uint32_t chunk_len);
+dsg_status dsg_get_tuning(uint32_t* block, uint32_t* blocks_per_sm, uint32_t* short_max, uint32_t* chunk_len);
+
+/* Upper bound (ns) on every device-side wait (grid barriers, queue polls).
+ * A wait that runs out makes its kernel return and the call report
+ * DSG_ETIMEOUT.  0 restores the default (10 s, or DSG_WAIT_LIMIT_NS). */
+void dsg_set_wait_limit_ns(uint64_t ns);
+
+/*
+ * Fault-detection probe.  Launches a kernel whose bounded wait can never be
+ * satisfied -- which = 0: one thread polls a device flag that nothing sets;
+ * which = 1: a two-block cooperative grid where one block skips the grid
+ * barrier the other waits in -- and returns the status the library's own
+ * time-out path produces (DSG_ETIMEOUT after limit_ns, 0 < limit_ns <= 10 s).
+ * No fault, trap or unbounded spin is involved.
+ */
+dsg_status dsg_debug_wait_timeout(uint32_t which, uint64_t limit_ns);
+
+/* ------------------------------------------------------- launch accounting */
+
+/* Number of kernels this library has launched in the process. */
+unsigned long long dsg_launch_count(void);
+/* With profiling on, every launch is bracketed by CUDA events on the stream
+ * it runs on; dsg_profile_report writes one line "kernel launches total_ms"
+ * per kernel into buf (at most cap bytes) and returns the kernel count. */
+void dsg_profile_enable(int on);
+void dsg_profile_reset(void);
+int dsg_profile_report(char* buf, size_t cap);
+
+/* ------------------------------------------------------------- errors */
+
+const char* dsg_status_string(dsg_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* dsg_last_error(void);
+
+/* Library version string. */
+const char* dsg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSG_H */

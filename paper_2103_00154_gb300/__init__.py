@@ -1,0 +1,189 @@
+"""GB300-native densest-subgraph peeling (arXiv 2103.00154 hot path).
+
+Thin Python face of libdsg (see include/dsg.h).  Names follow the C ABI:
+
+    g = Graph.from_edges(n, src, dst)        # dsg_graph_from_edges (ingest)
+    g = Graph.from_csr(n, off, adj)          # dsg_graph_from_csr
+    mask, E, V = g.bahmani(p, q)             # dsg_bahmani (Algorithm 1)
+    tr = g.bahmani_trace(p, q)               # dsg_bahmani_trace
+    core = g.kcore()                         # dsg_kcore (Algorithm 2, phase 1)
+
+Inputs and outputs may be numpy arrays (host) or torch tensors (host or
+CUDA).  PyTorch is used only for device memory and streams; all work runs in
+libdsg's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native as N
+from ._native import (DSG_CSR_CANONICALIZE, DSG_CSR_VALIDATE, DSG_PTRS_DEVICE, DsgError,  # noqa: F401
+                      lib)
+
+__all__ = ["Graph", "Trace", "DsgError", "lib", "round_bound", "set_tuning", "get_tuning", "set_wait_limit_ns",
+           "DSG_CSR_CANONICALIZE", "DSG_CSR_VALIDATE", "DSG_PTRS_DEVICE"]
+
+
+def round_bound(n: int, p: int, q: int) -> int:
+    return int(lib().dsg_round_bound(n, p, q))
+
+
+def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, chunk_len: int = 256):
+    N.check(lib().dsg_set_tuning(block, blocks_per_sm, short_max, chunk_len), "set_tuning")
+
+
+def get_tuning():
+    v = [ctypes.c_uint32() for _ in range(4)]
+    N.check(lib().dsg_get_tuning(*[ctypes.byref(x) for x in v]), "get_tuning")
+    return dict(zip(("block", "blocks_per_sm", "short_max", "chunk_len"), (x.value for x in v)))
+
+
+def set_wait_limit_ns(ns: int):
+    lib().dsg_set_wait_limit_ns(int(ns))
+
+
+@dataclass
+class Trace:
+    rounds: int
+    best_round: int
+    E: int
+    V: int
+    hist_S: np.ndarray
+    hist_E: np.ndarray
+    peel_round: object
+    mask: object
+    edges_scanned: int
+    decrements: int
+
+
+def _u32(x):
+    if isinstance(x, np.ndarray):
+        return np.ascontiguousarray(x, np.uint32)
+    return x
+
+
+def _u64(x):
+    if isinstance(x, np.ndarray):
+        return np.ascontiguousarray(x, np.uint64)
+    return x
+
+
+class Graph:
+    """A device-resident canonical graph (handle to dsg_graph)."""
+
+    def __init__(self, handle, keepalive=()):
+        self._h = handle
+        self._keep = keepalive  # device arrays borrowed with DSG_PTRS_DEVICE
+        n = ctypes.c_uint32()
+        m = ctypes.c_uint64()
+        N.check(lib().dsg_graph_info(self._h, ctypes.byref(n), ctypes.byref(m)), "graph_info")
+        self.n = n.value
+        self.m = m.value
+
+    # ------------------------------------------------------------ creation
+    @classmethod
+    def from_csr(cls, n: int, off, adj, flags: int = 0, stream=None) -> "Graph":
+        off, adj = _u64(off), _u32(adj)
+        h = ctypes.c_void_p()
+        keep = ()
+        if N.is_device(off):
+            flags |= DSG_PTRS_DEVICE if not (flags & DSG_CSR_CANONICALIZE) else 0
+            keep = (off, adj)
+        N.check(lib().dsg_graph_from_csr(n, N.ptr(off), N.ptr(adj), flags, N.stream_handle(stream),
+                                         ctypes.byref(h)), "graph_from_csr")
+        return cls(h, keep)
+
+    @classmethod
+    def from_edges(cls, n: int, src, dst, flags: int = 0, stream=None) -> "Graph":
+        src, dst = _u32(src), _u32(dst)
+        m_raw = int(src.shape[0])
+        if int(dst.shape[0]) != m_raw:
+            raise ValueError("src and dst differ in length")
+        if N.is_device(src):
+            flags |= DSG_PTRS_DEVICE
+        h = ctypes.c_void_p()
+        N.check(lib().dsg_graph_from_edges(n, m_raw, N.ptr(src) if m_raw else None, N.ptr(dst) if m_raw else None,
+                                           flags, N.stream_handle(stream), ctypes.byref(h)), "graph_from_edges")
+        return cls(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dsg_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        N.check(lib().dsg_graph_set_stream(self._h, N.stream_handle(stream)), "set_stream")
+
+    # ------------------------------------------------------------ queries
+    def csr(self):
+        off = np.empty(self.n + 1, np.uint64)
+        adj = np.empty(max(2 * self.m, 1), np.uint32)
+        N.check(lib().dsg_graph_csr(self._h, N.ptr(off), N.ptr(adj)), "graph_csr")
+        return off, adj[:2 * self.m]
+
+    def bahmani(self, p: int, q: int, out_set=None, want_set: bool = True):
+        """Algorithm 1 with eps = p/q.  Returns (mask, E, V)."""
+        if want_set and out_set is None:
+            out_set = np.empty(max(self.n, 1), np.uint8)
+        E = ctypes.c_uint64()
+        V = ctypes.c_uint64()
+        N.check(lib().dsg_bahmani(self._h, p, q, N.ptr(out_set) if want_set else None, ctypes.byref(E),
+                                  ctypes.byref(V)), "bahmani")
+        if isinstance(out_set, np.ndarray):
+            out_set = out_set[:self.n]
+        return out_set, E.value, V.value
+
+    def bahmani_trace(self, p: int, q: int, hist_cap: int | None = None, peel_round=None, out_set=None) -> Trace:
+        if hist_cap is None:
+            hist_cap = round_bound(self.n, p, q) + 1
+        hs = np.zeros(max(hist_cap, 1), np.uint64)
+        he = np.zeros(max(hist_cap, 1), np.uint64)
+        if peel_round is None:
+            peel_round = np.zeros(max(self.n, 1), np.uint32)
+        if out_set is None:
+            out_set = np.zeros(max(self.n, 1), np.uint8)
+        t = N.Trace(0, 0, 0, 0, hist_cap, N.ptr(hs), N.ptr(he), N.ptr(peel_round), N.ptr(out_set), 0, 0)
+        N.check(lib().dsg_bahmani_trace(self._h, p, q, ctypes.byref(t)), "bahmani_trace")
+        R = t.rounds
+        if isinstance(peel_round, np.ndarray):
+            peel_round = peel_round[:self.n]
+        if isinstance(out_set, np.ndarray):
+            out_set = out_set[:self.n]
+        return Trace(R, t.best_round, t.best_E, t.best_V, hs[:R + 1].copy(), he[:R + 1].copy(), peel_round,
+                     out_set, t.edges_scanned, t.decrements)
+
+    def kcore(self, out=None):
+        """Core numbers (Algorithm 2, first phase)."""
+        if out is None:
+            out = np.empty(max(self.n, 1), np.uint32)
+        N.check(lib().dsg_kcore(self._h, N.ptr(out)), "kcore")
+        if isinstance(out, np.ndarray):
+            out = out[:self.n]
+        return out
+
+    def kcore_counters(self, out=None):
+        """Core numbers plus the run's counters: levels, subrounds,
+        rem_scanned, rem_written, atomics."""
+        if out is None:
+            out = np.empty(max(self.n, 1), np.uint32)
+        st = np.zeros(5, np.uint64)
+        N.check(lib().dsg_kcore_stats(self._h, N.ptr(out), st.ctypes.data_as(N._U64P), 5), "kcore_stats")
+        if isinstance(out, np.ndarray):
+            out = out[:self.n]
+        keys = ("levels", "subrounds", "rem_scanned", "rem_written", "atomics")
+        return out, {k: int(v) for k, v in zip(keys, st)}

@@ -1,0 +1,152 @@
+// Shared pieces of the peel and core kernels: the frontier representation
+// (short rows listed by vertex, long rows cut into fixed-size chunk items),
+// the row scanner that walks a frontier's adjacency, and entry points shared
+// between translation units.
+#pragma once
+
+#include "dsg_common.cuh"
+
+namespace dsg {
+
+// Tuning knobs of the round kernels (see tune.cu for the defaults and the
+// autotuner that picks them).
+struct Tuning {
+    uint32_t block = 512;       // threads per block of the persistent kernels
+    uint32_t blocks_per_sm = 0; // 0: as many as fit
+    uint32_t short_max = 32;    // rows up to this length go through the tile path
+    uint32_t chunk_len = 256;   // long rows are cut into items of this many entries
+};
+
+Tuning current_tuning();
+
+// Counts one kernel launch and, when profiling is on, brackets it with CUDA
+// events on its stream.  Construct right before the launch, destroy right
+// after it:  { LaunchScope ls("name", s); kernel<<<...>>>(...); }
+class LaunchScope {
+  public:
+    LaunchScope(const char* name, cudaStream_t s);
+    ~LaunchScope();
+  private:
+    const char* name_;
+    cudaStream_t s_;
+    void* a_ = nullptr;
+    void* b_ = nullptr;
+    bool timed_ = false;
+};
+
+// Ingest raw pairs held in a CSR (each entry (v, adj[j]) is one pair).
+dsg_status ingest_from_csr_entries(uint32_t n, const uint64_t* off, const uint32_t* adj, uint64_t total,
+                                   uint32_t flags, cudaStream_t s, dsg_graph** out);
+
+// Device check that a graph is canonical (sorted rows, no loops, no repeats,
+// symmetric, ids < n).  DSG_EINVAL with a message if not.
+dsg_status validate_csr(const dsg_graph* g);
+
+// Grid size for a cooperative launch of `kernel` with `block` threads and
+// `smem` dynamic shared memory, capped so small problems use few blocks.
+template <class K>
+cudaError_t coop_grid(K kernel, uint32_t block, size_t smem, uint64_t work_items, uint32_t blocks_per_sm,
+                      uint32_t* grid) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)block, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (blocks_per_sm && (int)blocks_per_sm < per_sm) per_sm = (int)blocks_per_sm;
+    uint64_t g = (uint64_t)per_sm * (uint64_t)dev_info().sms;
+    uint64_t need = (work_items + block - 1) / block;
+    if (need < 1) need = 1;
+    if (g > need) g = need;
+    *grid = (uint32_t)g;
+    return cudaSuccess;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const unsigned long long* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Shared memory of one tile of the row scanner.
+template <int TB>
+struct TileSmem {
+    uint32_t start[TB];  // exclusive prefix of row lengths
+    uint64_t beg[TB];    // row start in adj
+    uint32_t v[TB];      // row owner
+    uint32_t scan_tmp[33];
+    uint64_t scan_tmp64[33];
+};
+
+// Walk every adjacency entry of a frontier.
+//   short rows: F[lo, hi), one vertex per entry; a block takes TB of them,
+//     prefix-sums their lengths and spreads the concatenated entries evenly
+//     over its threads (consecutive threads read consecutive entries).
+//   long rows: C[clo, chi), items (v << 32 | c) standing for entries
+//     [off[v] + c*chunk_len, min(off[v+1], off[v] + (c+1)*chunk_len)); one warp
+//     per item, 32 consecutive entries per step.
+// fn(u, v) is called once per entry (u = neighbour, v = row owner).
+template <int TB, class Fn>
+__device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
+                                              const uint32_t* __restrict__ F, uint64_t lo, uint64_t hi,
+                                              const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
+                                              uint32_t chunk_len, TileSmem<TB>& sm, Fn& fn, uint32_t dbg_n = 0) {
+    const uint32_t tid = threadIdx.x;
+    // ---- short rows, edge-balanced inside each tile
+    for (uint64_t t = lo + (uint64_t)blockIdx.x * TB; t < hi; t += (uint64_t)gridDim.x * TB) {
+        uint64_t i = t + tid;
+        uint32_t cnt = (uint32_t)min((uint64_t)TB, hi - t);
+        uint32_t v = 0, len = 0;
+        uint64_t b = 0;
+        if (tid < cnt) {
+            v = F[i];
+#ifdef DSG_DEBUG_BOUNDS
+            if (v >= dbg_n) { fn(0xfffffffeu, v); v = 0; }
+#endif
+            b = off[v];
+            len = (uint32_t)(off[v + 1] - b);
+        }
+        uint32_t total;
+        uint32_t st = block_excl_scan<uint32_t>(len, sm.scan_tmp, &total);
+        sm.start[tid] = st;
+        sm.beg[tid] = b;
+        sm.v[tid] = v;
+        __syncthreads();
+        for (uint32_t e = tid; e < total; e += TB) {
+            // owner = last row whose start is <= e
+            uint32_t a = 0, z = cnt;  // invariant: start[a] <= e, answer in [a, z)
+            while (z - a > 1) {
+                uint32_t mid = (a + z) >> 1;
+                if (sm.start[mid] <= e) a = mid; else z = mid;
+            }
+#ifdef DSG_DEBUG_BOUNDS
+            if (sm.beg[a] + (e - sm.start[a]) >= off[dbg_n]) { fn(0xffffffffu, 0xffffffffu); continue; }
+#endif
+            uint32_t u = adj[sm.beg[a] + (e - sm.start[a])];
+            fn(u, sm.v[a]);
+        }
+        __syncthreads();
+    }
+    // ---- long rows, one warp per chunk item
+    const uint32_t lane = tid & 31u;
+    const uint64_t gw = ((uint64_t)blockIdx.x * TB + tid) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * TB) >> 5;
+    for (uint64_t it = clo + gw; it < chi; it += nw) {
+        uint64_t item = C[it];
+        uint32_t v = (uint32_t)(item >> 32);
+#ifdef DSG_DEBUG_BOUNDS
+        if (v >= dbg_n) { fn(0xfffffffdu, v); continue; }
+#endif
+        uint64_t c = item & 0xffffffffull;
+        uint64_t b = off[v], e_end = off[v + 1];
+        uint64_t beg = b + c * chunk_len;
+        uint64_t end = min(e_end, beg + chunk_len);
+        for (uint64_t j = beg + lane; j < end; j += 32) fn(adj[j], v);
+    }
+}
+
+}  // namespace dsg

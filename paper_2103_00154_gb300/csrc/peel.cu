@@ -1,0 +1,356 @@
+// Algorithm 1 (P-Bahmani): the round-synchronous (2+2eps) densest-subgraph
+// peel as one persistent cooperative kernel.
+//
+// Per round r, with S_r and E_r = |E(S_r)| known to every block:
+//   phase 1 (Alg. 1 part 1, "parallel for v in active"): every alive vertex is
+//     tested against T_r = floor(2(p+q)E_r / (q|S_r|)), i.e. deg <= 2(1+eps)rho
+//     exactly; failures are marked and queued (short rows by vertex, long rows
+//     as chunk items), survivors are compacted into the next alive list
+//     (warp ballot + block scan + one atomic per block and list);
+//   grid barrier (Alg. 1 "barrier synchronization");
+//   phase 2 (Alg. 1 part 2): every adjacency entry u of every failed v is read
+//     once; an alive u loses one degree (atomicSub) and the edge counts as
+//     removed; an edge whose both ends failed this round counts once (u > v);
+//     block-reduced removal counts go to one global counter (Alg. 1 "reduce");
+//   grid barrier; every block derives S_{r+1}, E_{r+1} from the monotone
+//   counters; block 0 records the history and keeps the densest set (strict
+//   ">", Alg. 1 "if rho > rho~").
+//
+// Vertex state is one 32-bit word: an alive vertex holds its degree inside
+// S_r (< 2^31); a failed one holds 0x80000000 | (round it failed, 1-based).
+#include "dsg_common.cuh"
+#include "dsg_kernels.cuh"
+
+namespace dsg {
+
+constexpr uint32_t kDead = 0x80000000u;
+
+struct __align__(128) PeelCtl {
+    uint32_t bar;
+    uint32_t pad0[31];
+    uint32_t err;
+    uint32_t pad1[31];
+    unsigned long long failed;  // sum of |A_t|
+    unsigned long long pad2[15];
+    unsigned long long nshort;  // cursor of the short-row failed list
+    unsigned long long pad3[15];
+    unsigned long long nchunk;  // cursor of the chunk-item list
+    unsigned long long pad4[15];
+    unsigned long long surv;    // cursor of survivor writes (all rounds)
+    unsigned long long pad5[15];
+    unsigned long long dE;      // sum of removed edges
+    unsigned long long pad6[15];
+    unsigned long long dec;     // alive-neighbour decrements
+    unsigned long long pad7[15];
+    unsigned long long rounds, best_round, best_E, best_V;
+};
+
+struct PeelArgs {
+    uint32_t n;
+    uint64_t m;
+    uint64_t p, q;
+    const uint64_t* off;
+    const uint32_t* adj;
+    uint32_t* st;
+    uint32_t* listA;
+    uint32_t* listB;
+    uint32_t* F;
+    uint64_t* C;
+    uint64_t* hist_S;
+    uint64_t* hist_E;
+    uint64_t hist_cap;
+    PeelCtl* ctl;
+    uint64_t limit_ns;
+    uint32_t short_max;
+    uint32_t chunk_len;
+};
+
+// floor(2(p+q)E / (qS)) clamped to 32 bits; S > 0.
+__device__ __forceinline__ uint32_t peel_threshold(uint64_t p, uint64_t q, uint64_t E, uint64_t S) {
+    unsigned __int128 num = (unsigned __int128)2 * (unsigned __int128)(p + q) * (unsigned __int128)E;
+    unsigned __int128 den = (unsigned __int128)q * (unsigned __int128)S;
+    unsigned __int128 t = num / den;
+    return t > (unsigned __int128)0xffffffffu ? 0xffffffffu : (uint32_t)t;
+}
+
+template <int TB>
+struct PeelSmem {
+    TileSmem<TB> tile;
+    uint64_t bases[4];
+    uint64_t red[33];
+};
+
+template <int TB>
+__global__ void __launch_bounds__(TB) peel_kernel(PeelArgs a) {
+    __shared__ PeelSmem<TB> sm;
+    PeelCtl* ctl = a.ctl;
+    const uint32_t tid = threadIdx.x;
+    uint64_t S = a.n, E = a.m;
+    uint64_t r = 0;
+    uint64_t short_lo = 0, chunk_lo = 0, surv_base = 0;
+    const uint32_t* alive = nullptr;  // round 0: identity
+    uint32_t* next = a.listA;
+    uint64_t best_E = E, best_V = S, best_round = 0;
+    if (blockIdx.x == 0 && tid == 0) {
+        a.hist_S[0] = S;
+        a.hist_E[0] = E;
+    }
+    while (S > 0) {
+        const uint32_t T = peel_threshold(a.p, a.q, E, S);
+        const uint32_t mark = kDead | (uint32_t)(r + 1);
+        // ------------------------------------------------ phase 1: test + compact
+        for (uint64_t t = (uint64_t)blockIdx.x * TB; t < S; t += (uint64_t)gridDim.x * TB) {
+            uint64_t i = t + tid;
+            bool valid = i < S;
+            uint32_t v = 0, d = 0, nch = 0;
+            uint64_t len = 0;
+            bool fail = false;
+            if (valid) {
+                if (r == 0) {
+                    v = (uint32_t)i;
+                    len = a.off[v + 1] - a.off[v];
+                    d = (uint32_t)len;
+                } else {
+                    v = alive[i];
+                    d = a.st[v];
+                }
+                fail = d <= T;
+                if (fail) {
+                    if (r != 0) len = a.off[v + 1] - a.off[v];
+                    a.st[v] = mark;
+                    if (len > a.short_max) nch = (uint32_t)((len + a.chunk_len - 1) / a.chunk_len);
+                } else if (r == 0) {
+                    a.st[v] = d;
+                }
+            }
+            bool is_short = fail && nch == 0;
+            bool is_surv = valid && !fail;
+            // packed counts: short | surv << 16 | long-fail << 32
+            uint64_t pk = (uint64_t)is_short | ((uint64_t)is_surv << 16) | ((uint64_t)(nch > 0) << 32);
+            uint64_t pk_tot;
+            uint64_t pk_pre = block_excl_scan<uint64_t>(pk, sm.tile.scan_tmp64, &pk_tot);
+            uint32_t ch_tot;
+            uint32_t ch_pre = block_excl_scan<uint32_t>(nch, sm.tile.scan_tmp, &ch_tot);
+            if (tid == 0) {
+                uint64_t ns = pk_tot & 0xffff, nv = (pk_tot >> 16) & 0xffff, nl = (pk_tot >> 32) & 0xffff;
+                sm.bases[0] = ns ? atomicAdd(&ctl->nshort, ns) : 0;
+                sm.bases[1] = nv ? atomicAdd(&ctl->surv, nv) : 0;
+                sm.bases[2] = ch_tot ? atomicAdd(&ctl->nchunk, (unsigned long long)ch_tot) : 0;
+                if (ns + nl) atomicAdd(&ctl->failed, ns + nl);
+            }
+            __syncthreads();
+            if (is_short) a.F[sm.bases[0] + (pk_pre & 0xffff)] = v;
+            if (is_surv) next[sm.bases[1] - surv_base + ((pk_pre >> 16) & 0xffff)] = v;
+            if (nch) {
+                uint64_t c0 = sm.bases[2] + ch_pre;
+                for (uint32_t c = 0; c < nch; ++c) a.C[c0 + c] = ((uint64_t)v << 32) | c;
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+        const uint64_t failed_hi = ld_relaxed_u64(&ctl->failed);
+        const uint64_t short_hi = ld_relaxed_u64(&ctl->nshort);
+        const uint64_t chunk_hi = ld_relaxed_u64(&ctl->nchunk);
+        // ------------------------------------------------ phase 2: neighbour scan
+        uint64_t dE = 0, ndec = 0;
+        uint32_t* st = a.st;
+        auto visit = [&](uint32_t u, uint32_t v) {
+#ifdef DSG_DEBUG_BOUNDS
+            if (u >= a.n) { atomicOr(&ctl->err, ERR_RANGE); return; }
+#endif
+            uint32_t w = st[u];
+            if (!(w & kDead)) {
+                atomicSub(&st[u], 1u);
+                ++ndec;
+            } else if (w == mark && u > v) {
+                ++dE;
+            }
+        };
+        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, sm.tile,
+                          visit, a.n);
+        uint64_t bdec = block_sum<uint64_t>(ndec, sm.red);
+        uint64_t bdE = block_sum<uint64_t>(dE, sm.red) + bdec;
+        if (tid == 0 && bdE) atomicAdd(&ctl->dE, (unsigned long long)bdE);
+        if (tid == 0 && bdec) atomicAdd(&ctl->dec, (unsigned long long)bdec);
+        if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+        const uint64_t dE_tot = ld_relaxed_u64(&ctl->dE);
+        const uint64_t S1 = (uint64_t)a.n - failed_hi;
+        const uint64_t E1 = a.m - dE_tot;
+        ++r;
+        if (blockIdx.x == 0 && tid == 0) {
+            if (r < a.hist_cap) {
+                a.hist_S[r] = S1;
+                a.hist_E[r] = E1;
+            } else {
+                atomicOr(&ctl->err, ERR_CAPACITY);
+            }
+        }
+        if (S1 > 0 && (unsigned __int128)E1 * best_V > (unsigned __int128)best_E * S1) {
+            best_round = r;
+            best_E = E1;
+            best_V = S1;
+        }
+        surv_base += S1;
+        short_lo = short_hi;
+        chunk_lo = chunk_hi;
+        alive = next;
+        next = (next == a.listA) ? a.listB : a.listA;
+        S = S1;
+        E = E1;
+        if (r >= a.hist_cap) break;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl->rounds = r;
+        ctl->best_round = best_round;
+        ctl->best_E = best_E;
+        ctl->best_V = best_V;
+    }
+}
+
+// peel_round[v] = round v failed; set[v] = peel_round > best_round.
+__global__ void peel_finish_kernel(uint32_t n, const uint32_t* __restrict__ st, const PeelCtl* __restrict__ ctl,
+                                   uint32_t* __restrict__ peel_round, uint8_t* __restrict__ set) {
+    uint64_t br = ctl->best_round;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t pr = st[v] & ~kDead;
+        if (peel_round) peel_round[v] = pr;
+        if (set) set[v] = pr > br ? 1 : 0;
+    }
+}
+
+template <int TB>
+static cudaError_t launch_peel(PeelArgs& a, uint32_t blocks_per_sm, cudaStream_t s) {
+    uint32_t grid = 1;
+    cudaError_t e = coop_grid(peel_kernel<TB>, TB, 0, a.n, blocks_per_sm, &grid);
+    if (e != cudaSuccess) return e;
+    void* params[] = {&a};
+    LaunchScope ls("peel_rounds", s);
+    return cudaLaunchCooperativeKernel((const void*)peel_kernel<TB>, dim3(grid), dim3(TB), params, 0, s);
+}
+
+// Run the peel; results land in the returned control block and, if given,
+// in hist / peel_round / set (device pointers).
+static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t* hist_S_out, uint64_t* hist_E_out,
+                           uint64_t hist_cap_out, uint32_t* peel_round_out, uint8_t* set_out, PeelCtl* ctl_host) {
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    const Tuning tu = current_tuning();
+    memset(ctl_host, 0, sizeof(PeelCtl));
+    if (n == 0) {
+        static const uint64_t zero = 0;
+        if (hist_S_out && hist_cap_out) DSG_TRY_CUDA(copy_any(hist_S_out, &zero, sizeof(uint64_t), s));
+        if (hist_E_out && hist_cap_out) DSG_TRY_CUDA(copy_any(hist_E_out, &zero, sizeof(uint64_t), s));
+        DSG_TRY_CUDA(cudaStreamSynchronize(s));
+        return DSG_OK;
+    }
+    uint64_t cap = dsg_round_bound(n, p, q) + 1;
+    const uint64_t chunk_cap = (uint64_t)n + (2 * g->m) / tu.chunk_len + 1;
+    Scratch sc(s);
+    PeelArgs a;
+    a.n = n;
+    a.m = g->m;
+    a.p = p;
+    a.q = q;
+    a.off = g->off;
+    a.adj = g->adj;
+    a.hist_cap = cap;
+    a.limit_ns = wait_limit_ns();
+    a.short_max = tu.short_max;
+    a.chunk_len = tu.chunk_len;
+    DSG_TRY_CUDA(sc.get(&a.st, n));
+    DSG_TRY_CUDA(sc.get(&a.listA, n));
+    DSG_TRY_CUDA(sc.get(&a.listB, n));
+    DSG_TRY_CUDA(sc.get(&a.F, n));
+    DSG_TRY_CUDA(sc.get(&a.C, chunk_cap));
+    DSG_TRY_CUDA(sc.get(&a.hist_S, cap));
+    DSG_TRY_CUDA(sc.get(&a.hist_E, cap));
+    DSG_TRY_CUDA(sc.get(&a.ctl, 1));
+    DSG_TRY_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
+    cudaError_t e;
+    switch (tu.block) {
+        case 256: e = launch_peel<256>(a, tu.blocks_per_sm, s); break;
+        case 1024: e = launch_peel<1024>(a, tu.blocks_per_sm, s); break;
+        default: e = launch_peel<512>(a, tu.blocks_per_sm, s); break;
+    }
+    DSG_TRY_CUDA(e);
+    uint32_t* pr_dev = nullptr;
+    uint8_t* set_dev = nullptr;
+    bool pr_direct = peel_round_out && is_device_ptr(peel_round_out);
+    bool set_direct = set_out && is_device_ptr(set_out);
+    if (peel_round_out) {
+        if (pr_direct) pr_dev = peel_round_out;
+        else DSG_TRY_CUDA(sc.get(&pr_dev, n));
+    }
+    if (set_out) {
+        if (set_direct) set_dev = set_out;
+        else DSG_TRY_CUDA(sc.get(&set_dev, n));
+    }
+    if (pr_dev || set_dev) {
+        uint64_t want = ((uint64_t)n + 255) / 256, cap_b = (uint64_t)dev_info().sms * 8;
+        uint32_t blocks = (uint32_t)(want < cap_b ? want : cap_b);
+        {
+            LaunchScope ls("peel_finish", s);
+            peel_finish_kernel<<<blocks, 256, 0, s>>>(n, a.st, a.ctl, pr_dev, set_dev);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+    }
+    DSG_TRY_CUDA(cudaMemcpyAsync(ctl_host, a.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+    DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    dsg_status st = status_from_err(ctl_host->err, "bahmani peel");
+    if (st != DSG_OK) return st;
+    uint64_t R = ctl_host->rounds;
+    if (hist_S_out || hist_E_out) {
+        uint64_t k = R + 1 < hist_cap_out ? R + 1 : hist_cap_out;
+        if (hist_S_out) DSG_TRY_CUDA(copy_any(hist_S_out, a.hist_S, k * sizeof(uint64_t), s));
+        if (hist_E_out) DSG_TRY_CUDA(copy_any(hist_E_out, a.hist_E, k * sizeof(uint64_t), s));
+    }
+    if (peel_round_out && !pr_direct) DSG_TRY_CUDA(copy_any(peel_round_out, pr_dev, (size_t)n * 4, s));
+    if (set_out && !set_direct) DSG_TRY_CUDA(copy_any(set_out, set_dev, (size_t)n, s));
+    DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    return DSG_OK;
+}
+
+}  // namespace dsg
+
+using namespace dsg;
+
+extern "C" {
+
+dsg_status dsg_bahmani(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, uint8_t* out_set, uint64_t* out_E,
+                       uint64_t* out_V) {
+    clear_error();
+    DSG_CHECK_ARG(g, "graph is NULL");
+    DSG_CHECK_ARG(eps_den != 0, "eps_den must be positive");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    PeelCtl c;
+    dsg_status st = run_peel(g, eps_num, eps_den, nullptr, nullptr, 0, nullptr, out_set, &c);
+    if (st != DSG_OK) return st;
+    if (out_E) *out_E = g->n ? c.best_E : 0;
+    if (out_V) *out_V = g->n ? c.best_V : 0;
+    return DSG_OK;
+}
+
+dsg_status dsg_bahmani_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, dsg_trace* t) {
+    clear_error();
+    DSG_CHECK_ARG(g, "graph is NULL");
+    DSG_CHECK_ARG(t, "trace is NULL");
+    DSG_CHECK_ARG(eps_den != 0, "eps_den must be positive");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    PeelCtl c;
+    dsg_status st = run_peel(g, eps_num, eps_den, t->hist_S, t->hist_E, t->hist_cap, t->peel_round, t->out_set, &c);
+    if (st != DSG_OK) return st;
+    t->rounds = c.rounds;
+    t->best_round = c.best_round;
+    t->best_E = g->n ? c.best_E : 0;
+    t->best_V = g->n ? c.best_V : 0;
+    t->edges_scanned = 2 * g->m;
+    t->decrements = g->n ? c.dec : 0;
+    if (t->hist_cap < c.rounds + 1 && (t->hist_S || t->hist_E)) {
+        set_error("bahmani_trace: history needs %llu slots, got %llu", (unsigned long long)(c.rounds + 1),
+                  (unsigned long long)t->hist_cap);
+        return DSG_EOVERFLOW;
+    }
+    return DSG_OK;
+}
+
+}  // extern "C"
