@@ -136,6 +136,34 @@ dsg_status dsg_bahmani_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_
  * vertices), n + 1 when p == 0. */
 uint64_t dsg_round_bound(uint32_t n, uint32_t eps_num, uint32_t eps_den);
 
+/*
+ * dsg_bahmani without any device allocation.  The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory when they
+ * run the peel (their memory is reserved by an allocator they do not own, or
+ * their hot path must not call cudaMalloc, which can synchronise the device).
+ * It runs the same kernel as dsg_bahmani with every scratch array carved from
+ * one fixed 64 MiB buffer that this library keeps in device memory: the
+ * buffer is reserved on every GPU that loads the library and held until the
+ * process exits.
+ *   n, off, adj  canonical CSR in DEVICE memory (as dsg_graph_from_csr)
+ *   out_set      nullable, n bytes of DEVICE memory
+ *   out_E/out_V  nullable host pointers
+ *   stream       cudaStream_t to run on (NULL: default stream); the call
+ *                synchronises it before returning
+ * Limits: the scratch needs 16n bytes (alive lists, state, failed list) plus
+ * 8(n + 2m/chunk_len + 1) bytes (chunk items, chunk_len 256 by default) plus
+ * 16 * (dsg_round_bound(n, p, q) + 1) bytes (round history); a graph that
+ * needs more than 64 MiB is rejected with DSG_EINVAL before any GPU work
+ * (with eps > 0 that admits n up to about 2.7 million at m = 8n).
+ * The first call on a device looks the buffer's address up (once per
+ * device, with that device current); make that first call before any CUDA
+ * stream capture.  All calls share the one buffer and it keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ */
+dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const uint32_t* adj, uint32_t eps_num,
+                               uint32_t eps_den, uint8_t* out_set, uint64_t* out_E, uint64_t* out_V, void* stream);
+
 /* --------------------------------------------- Algorithm 2, first phase */
 
 /*

@@ -51,6 +51,7 @@ _SIGS = [
     ("dsg_bahmani", c.c_int, [_VP, c.c_uint32, c.c_uint32, _VP, _U64P, _U64P]),
     ("dsg_bahmani_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, c.POINTER(Trace)]),
     ("dsg_round_bound", c.c_uint64, [c.c_uint32, c.c_uint32, c.c_uint32]),
+    ("dsg_bahmani_noalloc", c.c_int, [c.c_uint32, _VP, _VP, c.c_uint32, c.c_uint32, _VP, _U64P, _U64P, _VP]),
     ("dsg_kcore", c.c_int, [_VP, _VP]),
     ("dsg_kcore_stats", c.c_int, [_VP, _VP, _U64P, c.c_uint32]),
     ("dsg_set_tuning", c.c_int, [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32]),

@@ -354,3 +354,142 @@ dsg_status dsg_bahmani_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_
 }
 
 }  // extern "C"
+
+// ===================================================== no-allocation variant
+//
+// Some callers cannot allocate device memory at the moment they want a peel:
+// code running under an allocator they do not own (a host application whose
+// memory pool is reserved up front, a framework that forbids allocation on
+// its hot path), or code that must not risk cudaMalloc's implicit device
+// synchronisation.  dsg_bahmani_noalloc serves them: it runs the same
+// persistent peel kernel as dsg_bahmani, but every scratch array lives in one
+// fixed buffer that belongs to this library file -- a static device array of
+// kNoAllocScratchBytes, reserved on each GPU that loads this code and held
+// until the process exits.  The caller passes the graph and the outputs.
+#include <mutex>
+
+namespace dsg {
+
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB per device
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, per device.  Host code may not use the
+// symbol itself as an address (on the host it names a shadow variable), so
+// the address is looked up once per device with cudaGetSymbolAddress.
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_addr[64];
+
+static dsg_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    DSG_TRY_CUDA(cudaGetDevice(&dev));
+    DSG_CHECK_ARG(dev >= 0 && dev < 64, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("bahmani_noalloc: cudaGetSymbolAddress of the static scratch failed: %s",
+                      cudaGetErrorString(e));
+            return DSG_ECUDA;
+        }
+        g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return DSG_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <int TB>
+static cudaError_t launch_peel_noalloc(PeelArgs& a, uint32_t blocks_per_sm, cudaStream_t s) {
+    uint32_t grid = 1;
+    cudaError_t e = coop_grid(peel_kernel<TB>, TB, 0, a.n, blocks_per_sm, &grid);
+    if (e != cudaSuccess) return e;
+    void* params[] = {&a};
+    return cudaLaunchCooperativeKernel((const void*)peel_kernel<TB>, dim3(grid), dim3(TB), params, 0, s);
+}
+
+}  // namespace dsg
+
+extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const uint32_t* adj, uint32_t eps_num,
+                                          uint32_t eps_den, uint8_t* out_set, uint64_t* out_E, uint64_t* out_V,
+                                          void* stream) {
+    clear_error();
+    DSG_CHECK_ARG(eps_den != 0, "eps_den must be positive");
+    DSG_CHECK_ARG(n < 0x80000000u, "n must be below 2^31");
+    DSG_CHECK_ARG(off && is_device_ptr(off), "off must be a device pointer");
+    DSG_CHECK_ARG(!out_set || is_device_ptr(out_set), "out_set must be a device pointer (or NULL)");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t total = 0;
+    DSG_TRY_CUDA(cudaMemcpyAsync(&total, off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    DSG_CHECK_ARG(total % 2 == 0, "off[n] must be even for a symmetric CSR");
+    DSG_CHECK_ARG(total == 0 || (adj && is_device_ptr(adj)), "adj must be a device pointer");
+    if (n == 0) {
+        if (out_E) *out_E = 0;
+        if (out_V) *out_V = 0;
+        return DSG_OK;
+    }
+    const Tuning tu = current_tuning();
+    const uint64_t m = total / 2;
+    const uint64_t cap = dsg_round_bound(n, eps_num, eps_den) + 1;
+    const uint64_t chunk_cap = (uint64_t)n + (2 * m) / tu.chunk_len + 1;
+    const size_t b_list = align256((size_t)n * 4);
+    const size_t b_chunk = align256((size_t)chunk_cap * 8);
+    const size_t b_hist = align256((size_t)cap * 8);
+    const size_t b_ctl = align256(sizeof(PeelCtl));
+    const size_t need = 4 * b_list + b_chunk + 2 * b_hist + b_ctl;
+    if (need > kNoAllocScratchBytes) {
+        set_error("bahmani_noalloc: this graph needs %zu bytes of scratch, above the fixed %zu-byte buffer "
+                  "(use dsg_bahmani)", need, (size_t)kNoAllocScratchBytes);
+        return DSG_EINVAL;
+    }
+    unsigned char* base = nullptr;
+    dsg_status st = noalloc_scratch(&base);
+    if (st != DSG_OK) return st;
+    PeelArgs a;
+    a.n = n;
+    a.m = m;
+    a.p = eps_num;
+    a.q = eps_den;
+    a.off = off;
+    a.adj = adj;
+    size_t o = 0;
+    a.st = reinterpret_cast<uint32_t*>(base + o); o += b_list;
+    a.listA = reinterpret_cast<uint32_t*>(base + o); o += b_list;
+    a.listB = reinterpret_cast<uint32_t*>(base + o); o += b_list;
+    a.F = reinterpret_cast<uint32_t*>(base + o); o += b_list;
+    a.C = reinterpret_cast<uint64_t*>(base + o); o += b_chunk;
+    a.hist_S = reinterpret_cast<uint64_t*>(base + o); o += b_hist;
+    a.hist_E = reinterpret_cast<uint64_t*>(base + o); o += b_hist;
+    a.ctl = reinterpret_cast<PeelCtl*>(base + o);
+    a.hist_cap = cap;
+    a.limit_ns = wait_limit_ns();
+    a.short_max = tu.short_max;
+    a.chunk_len = tu.chunk_len;
+    // The buffer keeps whatever the previous call left; only the control
+    // block must start at zero (every other array is written before it is read).
+    DSG_TRY_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
+    cudaError_t e;
+    switch (tu.block) {
+        case 256: e = launch_peel_noalloc<256>(a, tu.blocks_per_sm, s); break;
+        case 1024: e = launch_peel_noalloc<1024>(a, tu.blocks_per_sm, s); break;
+        default: e = launch_peel_noalloc<512>(a, tu.blocks_per_sm, s); break;
+    }
+    DSG_TRY_CUDA(e);
+    if (out_set) {
+        uint64_t want = ((uint64_t)n + 255) / 256, cap_b = (uint64_t)dev_info().sms * 8;
+        uint32_t blocks = (uint32_t)(want < cap_b ? want : cap_b);
+        peel_finish_kernel<<<blocks, 256, 0, s>>>(n, a.st, a.ctl, nullptr, out_set);
+        DSG_TRY_CUDA(cudaGetLastError());
+    }
+    PeelCtl c;
+    DSG_TRY_CUDA(cudaMemcpyAsync(&c, a.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+    DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    st = status_from_err(c.err, "bahmani_noalloc");
+    if (st != DSG_OK) return st;
+    if (out_E) *out_E = c.best_E;
+    if (out_V) *out_V = c.best_V;
+    return DSG_OK;
+}
