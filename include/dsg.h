@@ -197,6 +197,17 @@ dsg_status dsg_kcore_stats(const dsg_graph* g, uint32_t* out_core, uint64_t* sta
  */
 dsg_status dsg_set_tuning(uint32_t block, uint32_t blocks_per_sm, uint32_t short_max, uint32_t chunk_len);
 dsg_status dsg_get_tuning(uint32_t* block, uint32_t* blocks_per_sm, uint32_t* short_max, uint32_t* chunk_len);
+/* Degree at or above which decrements of a vertex are first combined in a
+ * per-block shared-memory table (one global atomic per block and phase for a
+ * hub instead of one per edge).  Default 64; DSG_HOT_DEG.  Results never
+ * depend on it. */
+dsg_status dsg_set_hot_degree(uint32_t hot_deg);
+/* Core numbers: a vertex whose row has at most local_max entries and that
+ * reaches the current level while a block drains is drained by that block
+ * in the same sub-round (PKC's thread-local buffer); longer rows go to the
+ * grid-wide frontier.  Default 1024; DSG_LOCAL_MAX.  Results never depend
+ * on it. */
+dsg_status dsg_set_local_max(uint32_t local_max);
 
 /* Upper bound (ns) on every device-side wait (grid barriers, queue polls).
  * A wait that runs out makes its kernel return and the call report
@@ -212,6 +223,25 @@ void dsg_set_wait_limit_ns(uint64_t ns);
  * No fault, trap or unbounded spin is involved.
  */
 dsg_status dsg_debug_wait_timeout(uint32_t which, uint64_t limit_ns);
+
+/*
+ * Analysis probes (no counterpart in the paper; used to measure the round
+ * machinery, not part of the method).
+ *   dsg_debug_peel_trace   one Algorithm 1 run recording %globaltimer (ns)
+ *                          at kernel start and after every grid barrier
+ *                          (2 per round) into ts[cap]; *count = stamps taken
+ *   dsg_debug_kcore_trace  one core decomposition recording pairs
+ *                          (ns, kind << 32 | k), kind 0 start, 1 init,
+ *                          2 level scan, 3 drain sub-round; *count = pairs
+ *   dsg_debug_barrier_ns   average latency of one grid barrier of a
+ *                          co-resident grid (block threads, blocks_per_sm,
+ *                          0 = occupancy limit) over iters barriers
+ */
+dsg_status dsg_debug_peel_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, uint64_t* ts, uint64_t cap,
+                                uint64_t* count);
+dsg_status dsg_debug_kcore_trace(const dsg_graph* g, uint64_t* ts, uint64_t cap, uint64_t* count);
+dsg_status dsg_debug_barrier_ns(uint32_t block, uint32_t blocks_per_sm, uint32_t iters, double* ns,
+                                uint32_t* grid_out);
 
 /* ------------------------------------------------------- launch accounting */
 

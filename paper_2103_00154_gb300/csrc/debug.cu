@@ -48,9 +48,52 @@ static dsg_status run_debug(int which, uint64_t limit_ns) {
     return status_from_err(h.err, which == 0 ? "debug flag wait" : "debug straggler barrier");
 }
 
+__global__ void barrier_loop_kernel(DebugCtl* c, uint32_t iters, uint64_t limit_ns) {
+    for (uint32_t i = 0; i < iters; ++i)
+        if (!grid_barrier(&c->bar, &c->err, limit_ns)) return;
+}
+
 }  // namespace dsg
 
 using namespace dsg;
+
+// Grid-barrier latency of a co-resident grid of `block`-thread blocks,
+// blocks_per_sm per SM (0 = as many as fit): average ns per barrier over
+// `iters` barriers, timed with CUDA events.
+extern "C" dsg_status dsg_debug_barrier_ns(uint32_t block, uint32_t blocks_per_sm, uint32_t iters, double* ns,
+                                           uint32_t* grid_out) {
+    clear_error();
+    DSG_CHECK_ARG(ns && iters > 0 && iters <= 1000000, "ns / iters");
+    DSG_CHECK_ARG(block >= 32 && block <= 1024 && block % 32 == 0, "block");
+    cudaStream_t s = nullptr;
+    Scratch sc(s);
+    DebugCtl* c;
+    DSG_TRY_CUDA(sc.get(&c, 1));
+    DSG_TRY_CUDA(cudaMemsetAsync(c, 0, sizeof(DebugCtl), s));
+    int per_sm = 0;
+    DSG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_loop_kernel, (int)block, 0));
+    if (blocks_per_sm && (int)blocks_per_sm < per_sm) per_sm = (int)blocks_per_sm;
+    uint32_t grid = (uint32_t)per_sm * (uint32_t)dev_info().sms;
+    uint64_t lim = wait_limit_ns();
+    void* params[] = {&c, &iters, &lim};
+    cudaEvent_t e0, e1;
+    DSG_TRY_CUDA(cudaEventCreate(&e0));
+    DSG_TRY_CUDA(cudaEventCreate(&e1));
+    DSG_TRY_CUDA(cudaEventRecord(e0, s));
+    DSG_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)barrier_loop_kernel, dim3(grid), dim3(block), params, 0, s));
+    DSG_TRY_CUDA(cudaEventRecord(e1, s));
+    DSG_TRY_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    DebugCtl h;
+    DSG_TRY_CUDA(cudaMemcpy(&h, c, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.err) return status_from_err(h.err, "barrier loop");
+    *ns = (double)ms * 1e6 / iters;
+    if (grid_out) *grid_out = grid;
+    return DSG_OK;
+}
 
 extern "C" dsg_status dsg_debug_wait_timeout(uint32_t which, uint64_t limit_ns) {
     clear_error();

@@ -15,6 +15,8 @@ struct Tuning {
     uint32_t blocks_per_sm = 0; // 0: as many as fit
     uint32_t short_max = 32;    // rows up to this length go through the tile path
     uint32_t chunk_len = 256;   // long rows are cut into items of this many entries
+    uint32_t hot_deg = 64;      // decrements of vertices at or above this degree are combined in shared memory
+    uint32_t local_max = 1024;  // k-core: rows up to this length reached while draining stay in the block
 };
 
 Tuning current_tuning();
@@ -72,6 +74,42 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
     return v;
 }
 
+// Per-block table that combines degree decrements aimed at the same
+// high-degree vertex, so a hub adjacent to thousands of failing vertices
+// takes one global atomic per block and phase instead of one per edge.
+// Open addressing over kAggSlots (key, count) pairs; a full probe sequence
+// falls back to a direct global atomic.
+constexpr uint32_t kAggBits = 11;
+constexpr uint32_t kAggSlots = 1u << kAggBits;
+constexpr uint32_t kAggEmpty = 0xffffffffu;
+
+struct AggTable {
+    uint32_t key[kAggSlots];
+    uint32_t cnt[kAggSlots];
+};
+
+__device__ __forceinline__ void agg_clear(AggTable& t) {
+    for (uint32_t i = threadIdx.x; i < kAggSlots; i += blockDim.x) {
+        t.key[i] = kAggEmpty;
+        t.cnt[i] = 0;
+    }
+}
+
+// Adds one to u's slot; false if no slot could be claimed.
+__device__ __forceinline__ bool agg_add(AggTable& t, uint32_t u) {
+    uint32_t h = (u * 0x9E3779B1u) >> (32 - kAggBits);
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {
+        uint32_t s = (h + i) & (kAggSlots - 1);
+        uint32_t prev = atomicCAS(&t.key[s], kAggEmpty, u);
+        if (prev == kAggEmpty || prev == u) {
+            atomicAdd(&t.cnt[s], 1u);
+            return true;
+        }
+    }
+    return false;
+}
+
 // Shared memory of one tile of the row scanner.
 template <int TB>
 struct TileSmem {
@@ -82,22 +120,31 @@ struct TileSmem {
     uint64_t scan_tmp64[33];
 };
 
-// Walk every adjacency entry of a frontier.
+// Walk every adjacency entry of a frontier, handing entries to the visitor
+// four at a time per thread so the visitor can issue four independent loads
+// (then four independent atomics) before it waits on any of them.
 //   short rows: F[lo, hi), one vertex per entry; a block takes TB of them,
 //     prefix-sums their lengths and spreads the concatenated entries evenly
 //     over its threads (consecutive threads read consecutive entries).
 //   long rows: C[clo, chi), items (v << 32 | c) standing for entries
 //     [off[v] + c*chunk_len, min(off[v+1], off[v] + (c+1)*chunk_len)); one warp
-//     per item, 32 consecutive entries per step.
-// fn(u, v) is called once per entry (u = neighbour, v = row owner).
-template <int TB, class Fn>
+//     per item, 32 consecutive entries per step, four steps in flight.
+// fn(u[4], v[4], valid) is called with bit j of `valid` set for each filled
+// slot j (u = neighbour, v = row owner).
+// LOCAL = true: F is this block's own list (e.g. in shared memory) and only
+// this block walks it; C is ignored.
+constexpr uint32_t kBatch = 4;
+
+template <int TB, bool LOCAL = false, class Fn>
 __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
-                                              const uint32_t* __restrict__ F, uint64_t lo, uint64_t hi,
+                                              const uint32_t* F, uint64_t lo, uint64_t hi,
                                               const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
                                               uint32_t chunk_len, TileSmem<TB>& sm, Fn& fn, uint32_t dbg_n = 0) {
     const uint32_t tid = threadIdx.x;
+    const uint64_t t0 = LOCAL ? lo : lo + (uint64_t)blockIdx.x * TB;
+    const uint64_t tstep = LOCAL ? (uint64_t)TB : (uint64_t)gridDim.x * TB;
     // ---- short rows, edge-balanced inside each tile
-    for (uint64_t t = lo + (uint64_t)blockIdx.x * TB; t < hi; t += (uint64_t)gridDim.x * TB) {
+    for (uint64_t t = t0; t < hi; t += tstep) {
         uint64_t i = t + tid;
         uint32_t cnt = (uint32_t)min((uint64_t)TB, hi - t);
         uint32_t v = 0, len = 0;
@@ -105,7 +152,11 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
         if (tid < cnt) {
             v = F[i];
 #ifdef DSG_DEBUG_BOUNDS
-            if (v >= dbg_n) { fn(0xfffffffeu, v); v = 0; }
+            if (v >= dbg_n) {
+                uint32_t bu[kBatch] = {0xfffffffeu}, bv[kBatch] = {v};
+                fn(bu, bv, 1u);
+                v = 0;
+            }
 #endif
             b = off[v];
             len = (uint32_t)(off[v + 1] - b);
@@ -116,21 +167,34 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
         sm.beg[tid] = b;
         sm.v[tid] = v;
         __syncthreads();
-        for (uint32_t e = tid; e < total; e += TB) {
-            // owner = last row whose start is <= e
-            uint32_t a = 0, z = cnt;  // invariant: start[a] <= e, answer in [a, z)
-            while (z - a > 1) {
-                uint32_t mid = (a + z) >> 1;
-                if (sm.start[mid] <= e) a = mid; else z = mid;
-            }
+        for (uint32_t e0 = tid; e0 < total; e0 += kBatch * TB) {
+            uint32_t bu[kBatch], bv[kBatch], valid = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < kBatch; ++j) {
+                uint32_t e = e0 + j * TB;
+                bu[j] = 0;
+                bv[j] = 0;
+                if (e < total) {
+                    // owner = last row whose start is <= e
+                    uint32_t a = 0, z = cnt;
+                    while (z - a > 1) {
+                        uint32_t mid = (a + z) >> 1;
+                        if (sm.start[mid] <= e) a = mid; else z = mid;
+                    }
+                    uint64_t pos = sm.beg[a] + (e - sm.start[a]);
 #ifdef DSG_DEBUG_BOUNDS
-            if (sm.beg[a] + (e - sm.start[a]) >= off[dbg_n]) { fn(0xffffffffu, 0xffffffffu); continue; }
+                    if (pos >= off[dbg_n]) { bu[j] = 0xffffffffu; bv[j] = 0xffffffffu; valid |= 1u << j; continue; }
 #endif
-            uint32_t u = adj[sm.beg[a] + (e - sm.start[a])];
-            fn(u, sm.v[a]);
+                    bu[j] = adj[pos];
+                    bv[j] = sm.v[a];
+                    valid |= 1u << j;
+                }
+            }
+            fn(bu, bv, valid);
         }
         __syncthreads();
     }
+    if (LOCAL) return;
     // ---- long rows, one warp per chunk item
     const uint32_t lane = tid & 31u;
     const uint64_t gw = ((uint64_t)blockIdx.x * TB + tid) >> 5;
@@ -139,13 +203,30 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
         uint64_t item = C[it];
         uint32_t v = (uint32_t)(item >> 32);
 #ifdef DSG_DEBUG_BOUNDS
-        if (v >= dbg_n) { fn(0xfffffffdu, v); continue; }
+        if (v >= dbg_n) {
+            uint32_t bu[kBatch] = {0xfffffffdu}, bv[kBatch] = {v};
+            fn(bu, bv, 1u);
+            continue;
+        }
 #endif
         uint64_t c = item & 0xffffffffull;
         uint64_t b = off[v], e_end = off[v + 1];
         uint64_t beg = b + c * chunk_len;
         uint64_t end = min(e_end, beg + chunk_len);
-        for (uint64_t j = beg + lane; j < end; j += 32) fn(adj[j], v);
+        for (uint64_t j0 = beg + lane; j0 < end; j0 += 32 * kBatch) {
+            uint32_t bu[kBatch], bv[kBatch], valid = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < kBatch; ++j) {
+                uint64_t jj = j0 + 32 * j;
+                bu[j] = 0;
+                bv[j] = v;
+                if (jj < end) {
+                    bu[j] = adj[jj];
+                    valid |= 1u << j;
+                }
+            }
+            fn(bu, bv, valid);
+        }
     }
 }
 

@@ -5,14 +5,20 @@
 //   2. scan    row starts of the (still repeated) entries
 //   3. scatter each pair is written into both rows
 //   4. sort    each row sorted and de-duplicated in place; rows are binned by
-//              length: <= 32 entries one warp (register bitonic network),
-//              <= kMidMax one block (shared-memory bitonic), longer rows one
-//              block each (shared-memory sorted runs + merge-path passes)
+//              length: <= 32 entries one warp, one value per lane; <= 1024
+//              one warp holding up to 32 values per lane (register bitonic
+//              network, no shared memory); <= 8192 one block (each warp sorts
+//              1024 values in registers, cross-warp merge steps go through
+//              shared memory); longer ("giant") rows are split by value
+//              window and each window is de-duplicated and ordered through a
+//              shared-memory bitmap
 //   5. scan    final row lengths -> off
 //   6. copy    unique entries into adj
 // The result is byte-identical to sorting the (min, max) keys and removing
 // repeats, because a canonical CSR of a given edge set is unique.
 #include <cooperative_groups.h>
+
+#include <algorithm>
 
 #include "dsg_common.cuh"
 #include "dsg_kernels.cuh"
@@ -22,18 +28,35 @@ namespace cg = cooperative_groups;
 namespace dsg {
 
 constexpr uint32_t kPad = 0xffffffffu;
-constexpr uint32_t kMidMax = 4096;   // longest row sorted in one shared-memory pass
-constexpr uint32_t kMidThreads = 512;
 constexpr uint32_t kScanTile = 2048;
+constexpr uint32_t kBlockRowMax = 8192;  // longest row sorted by one block
+constexpr uint32_t kBlockWarps = kBlockRowMax / 1024;
+constexpr uint32_t kWinBits = 13;        // giant rows: value windows of 8192 ids
+constexpr uint32_t kWin = 1u << kWinBits;
+constexpr uint32_t kWinWords = kWin / 32;
+constexpr int kClasses = 7;              // 0..4: warp rows E = 2..32, 5: block rows, 6: giant rows
 
 __global__ void validate_off_kernel(uint32_t n, const uint64_t* __restrict__ off, uint32_t* bad);
 
 struct IngestCtl {
     uint32_t err;
-    uint32_t n_mid;
-    uint32_t n_big;
+    uint32_t cls_count[kClasses];   // rows per sort class
+    uint32_t cls_fill[kClasses];    // list cursors
     uint32_t pad;
+    unsigned long long giant_entries;
 };
+
+// sort class of a row of raw length len (-1: at most 32 entries)
+__device__ __forceinline__ int row_class(uint32_t len) {
+    if (len <= 32) return -1;
+    if (len <= 64) return 0;
+    if (len <= 128) return 1;
+    if (len <= 256) return 2;
+    if (len <= 512) return 3;
+    if (len <= 1024) return 4;
+    if (len <= kBlockRowMax) return 5;
+    return 6;
+}
 
 // ----------------------------------------------------------- device scan
 
@@ -126,180 +149,356 @@ __global__ void scatter_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __res
 
 // ----------------------------------------------------------- row sort
 
-// Rows of <= 32 entries: one warp per row, register bitonic sort, dedup by
-// neighbour compare; longer rows are appended to the mid / big lists.
+__global__ void classify_count(uint32_t n, const uint32_t* __restrict__ cnt, IngestCtl* ctl) {
+    __shared__ uint32_t c[kClasses];
+    __shared__ unsigned long long giant;
+    if (threadIdx.x < kClasses) c[threadIdx.x] = 0;
+    if (threadIdx.x == 0) giant = 0;
+    __syncthreads();
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t len = cnt[v];
+        int k = row_class(len);
+        if (k >= 0) atomicAdd(&c[k], 1u);
+        if (k == 6) atomicAdd(&giant, (unsigned long long)len);
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses && c[threadIdx.x]) atomicAdd(&ctl->cls_count[threadIdx.x], c[threadIdx.x]);
+    if (threadIdx.x == 0 && giant) atomicAdd(&ctl->giant_entries, giant);
+}
+
+struct ClassLists {
+    uint32_t* rows;             // all class lists, back to back
+    uint32_t base[kClasses];    // start of each class in rows
+};
+
+// Rows of <= 32 entries: one warp per row, one value per lane, bitonic
+// network over shuffles, dedup by comparing with the previous lane.  Longer
+// rows are appended to their class list (warp-aggregated per class).
 __global__ void sort_small_rows(uint32_t n, const uint64_t* __restrict__ start, const uint32_t* __restrict__ cnt,
-                                uint32_t* __restrict__ tmp, uint32_t* __restrict__ newlen,
-                                uint32_t* __restrict__ mid_list, uint32_t* __restrict__ big_list, IngestCtl* ctl) {
+                                uint32_t* __restrict__ tmp, uint32_t* __restrict__ newlen, ClassLists lists,
+                                IngestCtl* ctl) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t v = gw; v < n; v += nw) {
-        uint32_t len = cnt[v];
-        if (len > 32) {
-            if (lane == 0) {
-                if (len <= kMidMax) mid_list[atomicAdd(&ctl->n_mid, 1u)] = (uint32_t)v;
-                else big_list[atomicAdd(&ctl->n_big, 1u)] = (uint32_t)v;
+    // one warp walks 32 rows at a time for the class append, then sorts its small rows
+    for (uint64_t v0 = gw * 32; v0 < n; v0 += nw * 32) {
+        uint64_t vl = v0 + lane;
+        uint32_t mylen = vl < n ? cnt[vl] : 0;
+        int cls = vl < n ? row_class(mylen) : -1;
+        uint32_t same = __match_any_sync(kFullMask, cls);
+        if (cls >= 0) {
+            uint32_t leader = __ffs(same) - 1;
+            uint32_t b = 0;
+            if (lane == leader) b = atomicAdd(&ctl->cls_fill[cls], (uint32_t)__popc(same));
+            b = __shfl_sync(same, b, leader);
+            lists.rows[lists.base[cls] + b + __popc(same & lanemask_lt())] = (uint32_t)vl;
+        }
+        uint32_t small = __ballot_sync(kFullMask, vl < n && cls < 0);
+        while (small) {
+            uint32_t src_lane = __ffs(small) - 1;
+            small &= small - 1;
+            uint64_t v = v0 + src_lane;
+            uint32_t len = __shfl_sync(kFullMask, mylen, src_lane);
+            if (len == 0) {
+                if (lane == 0) newlen[v] = 0;
+                continue;
             }
-            continue;
-        }
-        if (len == 0) {
-            if (lane == 0) newlen[v] = 0;
-            continue;
-        }
-        uint64_t b = start[v];
-        uint32_t x = lane < len ? tmp[b + lane] : kPad;
+            uint64_t b = start[v];
+            uint32_t x = lane < len ? tmp[b + lane] : kPad;
 #pragma unroll
-        for (uint32_t k = 2; k <= 32; k <<= 1) {
+            for (uint32_t k = 2; k <= 32; k <<= 1) {
 #pragma unroll
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                uint32_t y = __shfl_xor_sync(kFullMask, x, j);
-                bool up = (lane & k) == 0;
-                bool lower = (lane & j) == 0;
-                // lower lane keeps min when ascending, max when descending
-                x = (lower == up) ? min(x, y) : max(x, y);
-            }
-        }
-        uint32_t prev = __shfl_up_sync(kFullMask, x, 1);
-        bool keep = x != kPad && (lane == 0 || x != prev);
-        uint32_t bal = __ballot_sync(kFullMask, keep);
-        if (keep) tmp[b + __popc(bal & lanemask_lt())] = x;
-        if (lane == 0) newlen[v] = __popc(bal);
-    }
-}
-
-// Bitonic sort of `len` values in shared memory padded to a power of two `p2`.
-__device__ void smem_bitonic(uint32_t* s, uint32_t p2) {
-    for (uint32_t k = 2; k <= p2; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < p2; i += blockDim.x) {
-                uint32_t l = i ^ j;
-                if (l > i) {
-                    uint32_t a = s[i], b = s[l];
-                    bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        s[i] = b;
-                        s[l] = a;
-                    }
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    uint32_t y = __shfl_xor_sync(kFullMask, x, j);
+                    bool up = (lane & k) == 0;
+                    bool lower = (lane & j) == 0;
+                    // lower lane keeps min when ascending, max when descending
+                    x = (lower == up) ? min(x, y) : max(x, y);
                 }
             }
-            __syncthreads();
+            uint32_t prev = __shfl_up_sync(kFullMask, x, 1);
+            bool keep = x != kPad && (lane == 0 || x != prev);
+            uint32_t bal = __ballot_sync(kFullMask, keep);
+            if (keep) tmp[b + __popc(bal & lanemask_lt())] = x;
+            if (lane == 0) newlen[v] = __popc(bal);
         }
     }
 }
 
-// Keep the first of each run of equal values of sorted s[0, len) (no kPad
-// inside), writing them compacted to out; returns the kept count.
-__device__ uint32_t smem_unique_write(const uint32_t* s, uint32_t len, uint32_t* out, uint32_t* scan_tmp) {
-    uint32_t kept = 0;
-    for (uint32_t t = 0; t < len; t += blockDim.x) {
-        uint32_t i = t + threadIdx.x;
-        bool keep = i < len && (i == 0 || s[i] != s[i - 1]);
-        uint32_t tot;
-        uint32_t pre = block_excl_scan<uint32_t>(keep ? 1u : 0u, scan_tmp, &tot);
-        if (keep) out[kept + pre] = s[i];
-        kept += tot;
+// ---- bitonic network over values held in registers by one warp.
+// Value e of lane l has index base + 32e + l.  A compare-exchange at distance
+// J >= 32 pairs two registers of the same lane; J < 32 pairs two lanes.  The
+// direction of a pair is ascending when (index & k) == 0 (k = block size of
+// the current merge), as in the textbook network.
+template <int E, uint32_t J>
+__device__ __forceinline__ void bitonic_step(uint32_t (&x)[E], uint32_t base, uint32_t k, uint32_t lane) {
+    if constexpr (J >= 32) {
+        constexpr uint32_t je = J / 32;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if ((e & je) == 0) {
+                bool asc = ((base + (uint32_t)e * 32 + lane) & k) == 0;
+                uint32_t a = x[e], b = x[e | je];
+                x[e] = asc ? min(a, b) : max(a, b);
+                x[e | je] = asc ? max(a, b) : min(a, b);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            uint32_t y = __shfl_xor_sync(kFullMask, x[e], J);
+            bool asc = ((base + (uint32_t)e * 32 + lane) & k) == 0;
+            bool lower = (lane & J) == 0;
+            x[e] = (lower == asc) ? min(x[e], y) : max(x[e], y);
+        }
     }
-    return kept;
 }
 
-__global__ void __launch_bounds__(kMidThreads) sort_mid_rows(const uint32_t* __restrict__ list,
-                                                             const IngestCtl* __restrict__ ctl,
-                                                             const uint64_t* __restrict__ start,
-                                                             const uint32_t* __restrict__ cnt,
-                                                             uint32_t* __restrict__ tmp,
-                                                             uint32_t* __restrict__ newlen) {
-    __shared__ uint32_t s[kMidMax];
-    __shared__ uint32_t scan_tmp[33];
-    const uint32_t nmid = ctl->n_mid;
-    for (uint32_t r = blockIdx.x; r < nmid; r += gridDim.x) {
+// steps J, J/2, ..., 1 of a merge with block size k
+template <int E, uint32_t J>
+__device__ __forceinline__ void bitonic_merge(uint32_t (&x)[E], uint32_t base, uint32_t k, uint32_t lane) {
+    bitonic_step<E, J>(x, base, k, lane);
+    if constexpr (J > 1) bitonic_merge<E, J / 2>(x, base, k, lane);
+}
+
+// all merges k = 2, 4, ..., K: afterwards the warp's values are sorted, in
+// the direction the next merge (block size 2K) expects
+template <int E, uint32_t K>
+__device__ __forceinline__ void bitonic_sort(uint32_t (&x)[E], uint32_t base, uint32_t lane) {
+    if constexpr (K > 2) bitonic_sort<E, K / 2>(x, base, lane);
+    bitonic_merge<E, K / 2>(x, base, K, lane);
+}
+
+// Write the first of each run of equal sorted values (ascending, kPad last)
+// of the warp's registers to out[pos0 ...]; prev_in is the value before
+// index 0 (kPad if none).  Returns the number written.
+template <int E>
+__device__ __forceinline__ uint32_t warp_unique_write(const uint32_t (&x)[E], uint32_t prev_in, uint32_t lane,
+                                                      uint32_t* out) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        uint32_t up = __shfl_up_sync(kFullMask, x[e], 1);
+        uint32_t last_prev = e == 0 ? prev_in : __shfl_sync(kFullMask, x[e > 0 ? e - 1 : 0], 31);
+        uint32_t prev = lane == 0 ? last_prev : up;
+        bool keep = x[e] != kPad && x[e] != prev;
+        uint32_t bal = __ballot_sync(kFullMask, keep);
+        if (keep) out[pos + __popc(bal & lanemask_lt())] = x[e];
+        pos += __popc(bal);
+    }
+    return pos;
+}
+
+// Rows of 33..1024 entries: one warp per row, E values per lane.
+template <int E>
+__global__ void __launch_bounds__(256) sort_warp_rows(const uint32_t* __restrict__ list, uint32_t count,
+                                                      const uint64_t* __restrict__ start,
+                                                      const uint32_t* __restrict__ cnt, uint32_t* __restrict__ tmp,
+                                                      uint32_t* __restrict__ newlen) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = gw; r < count; r += nw) {
         uint32_t v = list[r];
         uint32_t len = cnt[v];
         uint64_t b = start[v];
-        uint32_t p2 = 64;
+        uint32_t x[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            uint32_t i = (uint32_t)e * 32 + lane;
+            x[e] = i < len ? tmp[b + i] : kPad;
+        }
+        bitonic_sort<E, 32 * E>(x, 0, lane);
+        uint32_t kept = warp_unique_write<E>(x, kPad, lane, tmp + b);
+        if (lane == 0) newlen[v] = kept;
+    }
+}
+
+// Rows of 1025..8192 entries: one block of 8 warps per row.  Each active warp
+// sorts 1024 values in registers; merges with block size 2048..p2 run their
+// cross-warp steps (distance >= 1024) through shared memory and the rest in
+// registers.
+__global__ void __launch_bounds__(kBlockWarps * 32) sort_block_rows(const uint32_t* __restrict__ list,
+                                                                    uint32_t count,
+                                                                    const uint64_t* __restrict__ start,
+                                                                    const uint32_t* __restrict__ cnt,
+                                                                    uint32_t* __restrict__ tmp,
+                                                                    uint32_t* __restrict__ newlen) {
+    __shared__ uint32_t s[kBlockRowMax];
+    __shared__ uint32_t wlast[kBlockWarps];
+    __shared__ uint32_t wcount[kBlockWarps];
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t base = w * 1024;
+    for (uint32_t r = blockIdx.x; r < count; r += gridDim.x) {
+        uint32_t v = list[r];
+        uint32_t len = cnt[v];
+        uint64_t b = start[v];
+        uint32_t p2 = 2048;
         while (p2 < len) p2 <<= 1;
-        for (uint32_t i = threadIdx.x; i < p2; i += blockDim.x) s[i] = i < len ? tmp[b + i] : kPad;
-        __syncthreads();
-        smem_bitonic(s, p2);
-        uint32_t kept = smem_unique_write(s, len, tmp + b, scan_tmp);
-        if (threadIdx.x == 0) newlen[v] = kept;
-        __syncthreads();
-    }
-}
-
-// Rows longer than kMidMax: one block per row.  Runs of kMidMax entries are
-// sorted in shared memory, then merged pairwise (merge path: each thread
-// binary-searches its diagonal and merges its share sequentially) between
-// tmp and the spare buffer until one run remains; finally de-duplicated.
-__device__ void merge_path_block(const uint32_t* A, uint32_t la, const uint32_t* B, uint32_t lb, uint32_t* out) {
-    uint32_t total = la + lb;
-    uint32_t per = (total + blockDim.x - 1) / blockDim.x;
-    uint32_t d0 = min(total, threadIdx.x * per), d1 = min(total, d0 + per);
-    // split of diagonal d: i from A, d - i from B, with A[i-1] <= B[d-i] and B[d-i-1] < A[i]
-    auto split = [&](uint32_t d) {
-        uint32_t lo = d > lb ? d - lb : 0, hi = min(d, la);
-        while (lo < hi) {
-            uint32_t i = (lo + hi) >> 1;
-            if (A[i] <= B[d - i - 1]) lo = i + 1; else hi = i;
+        const bool active = base < p2;
+        uint32_t x[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            uint32_t i = base + (uint32_t)e * 32 + lane;
+            x[e] = (active && i < len) ? tmp[b + i] : kPad;
         }
-        return lo;
-    };
-    uint32_t i = split(d0), j = d0 - i;
-    for (uint32_t d = d0; d < d1; ++d) {
-        if (j >= lb || (i < la && A[i] <= B[j])) out[d] = A[i++];
-        else out[d] = B[j++];
-    }
-}
-
-__global__ void __launch_bounds__(kMidThreads) sort_big_rows(const uint32_t* __restrict__ list,
-                                                             const IngestCtl* __restrict__ ctl,
-                                                             const uint64_t* __restrict__ start,
-                                                             const uint32_t* __restrict__ cnt,
-                                                             uint32_t* __restrict__ tmp, uint32_t* __restrict__ spare,
-                                                             uint32_t* __restrict__ newlen) {
-    __shared__ uint32_t s[kMidMax];
-    __shared__ uint32_t scan_tmp[33];
-    const uint32_t nbig = ctl->n_big;
-    for (uint32_t r = blockIdx.x; r < nbig; r += gridDim.x) {
-        uint32_t v = list[r];
-        uint32_t len = cnt[v];
-        uint64_t b = start[v];
-        uint32_t* src = tmp + b;
-        uint32_t* dst = spare + b;
-        // sorted runs of kMidMax
-        for (uint32_t r0 = 0; r0 < len; r0 += kMidMax) {
-            uint32_t l = min(kMidMax, len - r0);
-            for (uint32_t i = threadIdx.x; i < kMidMax; i += blockDim.x) s[i] = i < l ? src[r0 + i] : kPad;
-            __syncthreads();
-            smem_bitonic(s, kMidMax);
-            for (uint32_t i = threadIdx.x; i < l; i += blockDim.x) src[r0 + i] = s[i];
-            __syncthreads();
-        }
-        // merge passes
-        for (uint32_t run = kMidMax; run < len; run <<= 1) {
-            for (uint32_t a0 = 0; a0 < len; a0 += 2 * run) {
-                uint32_t la = min(run, len - a0);
-                uint32_t lb = a0 + run < len ? min(run, len - a0 - run) : 0;
-                merge_path_block(src + a0, la, src + a0 + la, lb, dst + a0);
+        if (active) bitonic_sort<32, 1024>(x, base, lane);
+        for (uint32_t k = 2048; k <= p2; k <<= 1) {
+            for (uint32_t j = k >> 1; j >= 1024; j >>= 1) {
+                if (active) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) s[base + (uint32_t)e * 32 + lane] = x[e];
+                }
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        uint32_t i = base + (uint32_t)e * 32 + lane;
+                        uint32_t y = s[i ^ j];
+                        bool asc = (i & k) == 0;
+                        bool lower = (i & j) == 0;
+                        x[e] = (lower == asc) ? min(x[e], y) : max(x[e], y);
+                    }
+                }
                 __syncthreads();
             }
-            uint32_t* t = src; src = dst; dst = t;
+            if (active) bitonic_merge<32, 512>(x, base, k, lane);
         }
-        // unique, in tiles, into tmp (src may be tmp or spare; writes trail reads)
-        uint32_t kept = 0;
-        for (uint32_t t0 = 0; t0 < len; t0 += blockDim.x) {
-            uint32_t i = t0 + threadIdx.x;
-            uint32_t x = i < len ? src[i] : 0;
-            bool keep = i < len && (i == 0 || x != src[i - 1]);
-            uint32_t tot;
-            uint32_t pre = block_excl_scan<uint32_t>(keep ? 1u : 0u, scan_tmp, &tot);
-            __syncthreads();
-            if (keep) tmp[b + kept + pre] = x;
-            kept += tot;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) newlen[v] = kept;
+        // de-duplicate across the block: each warp needs the previous warp's last value
+        if (lane == 31) wlast[w] = x[31];
         __syncthreads();
+        uint32_t prev_in = (w == 0 || !active) ? kPad : wlast[w - 1];
+        // count first, then write at the prefix of the warps' counts
+        uint32_t mine = 0;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            uint32_t up = __shfl_up_sync(kFullMask, x[e], 1);
+            uint32_t last_prev = e == 0 ? prev_in : __shfl_sync(kFullMask, x[e > 0 ? e - 1 : 0], 31);
+            uint32_t prev = lane == 0 ? last_prev : up;
+            mine += __popc(__ballot_sync(kFullMask, x[e] != kPad && x[e] != prev));
+        }
+        if (lane == 0) wcount[w] = active ? mine : 0;
+        __syncthreads();
+        uint32_t off = 0, total = 0;
+        for (uint32_t q = 0; q < kBlockWarps; ++q) {
+            if (q < w) off += wcount[q];
+            total += wcount[q];
+        }
+        if (active) warp_unique_write<32>(x, prev_in, lane, tmp + b + off);
+        if (threadIdx.x == 0) newlen[v] = total;
+        __syncthreads();
+    }
+}
+
+// ---- giant rows (> 8192 entries): partition each row by value window of
+// kWin ids (a counting sort on value >> kWinBits), then de-duplicate and order
+// each window with a kWin-bit bitmap in shared memory.
+
+// window histogram; grid.y walks giant rows, grid.x chunks of a row
+__global__ void giant_hist(const uint32_t* __restrict__ list, uint32_t count, const uint64_t* __restrict__ start,
+                           const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ tmp, uint32_t nwin,
+                           uint32_t* __restrict__ hist) {
+    extern __shared__ uint32_t sh[];
+    const bool use_smem = nwin <= 4096;
+    for (uint32_t r = blockIdx.y; r < count; r += gridDim.y) {
+        uint32_t v = list[r];
+        uint32_t len = cnt[v];
+        uint64_t b = start[v];
+        uint32_t* h = hist + (uint64_t)r * nwin;
+        if (use_smem) {
+            for (uint32_t i = threadIdx.x; i < nwin; i += blockDim.x) sh[i] = 0;
+            __syncthreads();
+        }
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+            uint32_t wv = tmp[b + i] >> kWinBits;
+            if (use_smem) atomicAdd(&sh[wv], 1u);
+            else atomicAdd(&h[wv], 1u);
+        }
+        if (use_smem) {
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < nwin; i += blockDim.x)
+                if (sh[i]) atomicAdd(&h[i], sh[i]);
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void giant_scatter(const uint32_t* __restrict__ list, uint32_t count, const uint64_t* __restrict__ start,
+                              const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ tmp, uint32_t nwin,
+                              const uint64_t* __restrict__ hoff, uint32_t* __restrict__ cursor,
+                              uint32_t* __restrict__ spare) {
+    for (uint32_t r = blockIdx.y; r < count; r += gridDim.y) {
+        uint32_t v = list[r];
+        uint32_t len = cnt[v];
+        uint64_t b = start[v];
+        const uint64_t* ho = hoff + (uint64_t)r * nwin;
+        uint32_t* cur = cursor + (uint64_t)r * nwin;
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+            uint32_t x = tmp[b + i];
+            uint32_t wv = x >> kWinBits;
+            spare[b + (ho[wv] - ho[0]) + atomicAdd(&cur[wv], 1u)] = x;
+        }
+    }
+}
+
+// one warp per (row, window); EMIT = false counts the window's distinct
+// values into ucnt, EMIT = true writes them in order at their row position
+template <bool EMIT>
+__global__ void __launch_bounds__(256) giant_windows(const uint32_t* __restrict__ list, uint32_t count,
+                                                     const uint64_t* __restrict__ start, uint32_t nwin,
+                                                     const uint32_t* __restrict__ hist,
+                                                     const uint64_t* __restrict__ hoff,
+                                                     const uint32_t* __restrict__ spare, uint32_t* __restrict__ ucnt,
+                                                     const uint64_t* __restrict__ uoff, uint32_t* __restrict__ tmp,
+                                                     uint32_t* __restrict__ newlen) {
+    __shared__ uint32_t bm[8][kWinWords];
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint64_t total = (uint64_t)count * nwin;
+    for (uint64_t it = (uint64_t)blockIdx.x * 8 + w; it < total; it += (uint64_t)gridDim.x * 8) {
+        uint32_t r = (uint32_t)(it / nwin), wi = (uint32_t)(it % nwin);
+        uint32_t v = list[r];
+        uint64_t b = start[v];
+        const uint64_t* ho = hoff + (uint64_t)r * nwin;
+        if (EMIT && wi == 0 && lane == 0) newlen[v] = (uint32_t)(uoff[(uint64_t)r * nwin + nwin] - uoff[(uint64_t)r * nwin]);
+        uint32_t h = hist[it];
+        if (h == 0) {
+            if (!EMIT && lane == 0) ucnt[it] = 0;  // every window's count feeds the scan
+            continue;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kWinWords / 32; ++q) bm[w][q * 32 + lane] = 0;
+        __syncwarp();
+        uint64_t seg = b + (ho[wi] - ho[0]);
+        for (uint32_t i = lane; i < h; i += 32) {
+            uint32_t x = spare[seg + i] & (kWin - 1);
+            atomicOr(&bm[w][x >> 5], 1u << (x & 31));
+        }
+        __syncwarp();
+        // lane owns words [lane * 8, lane * 8 + 8)
+        uint32_t words[kWinWords / 32], c = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < kWinWords / 32; ++q) {
+            words[q] = bm[w][lane * (kWinWords / 32) + q];
+            c += __popc(words[q]);
+        }
+        if (!EMIT) {
+            uint32_t tot = warp_sum(c);
+            if (lane == 0) ucnt[it] = tot;
+        } else {
+            uint32_t inc = warp_incl_scan(c);
+            uint64_t pos = b + (uoff[it] - uoff[(uint64_t)r * nwin]) + (inc - c);
+            uint32_t vbase = wi * kWin + lane * (kWinWords / 32) * 32;
+#pragma unroll
+            for (uint32_t q = 0; q < kWinWords / 32; ++q) {
+                uint32_t m = words[q];
+                while (m) {
+                    uint32_t bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    tmp[pos++] = vbase + q * 32 + bit;
+                }
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -336,7 +535,7 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     int dev = 0;
     DSG_TRY_CUDA(cudaGetDevice(&dev));
     Scratch sc(s);
-    uint32_t *cnt, *tmp, *spare, *newlen, *mid_list, *big_list;
+    uint32_t *cnt, *tmp, *newlen;
     uint64_t *start, *sums;
     IngestCtl* ctl;
     const uint64_t nt = (uint64_t)n / kScanTile + 2;
@@ -344,14 +543,14 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     DSG_TRY_CUDA(sc.get(&start, (size_t)n + 1));
     DSG_TRY_CUDA(sc.get(&sums, nt));
     DSG_TRY_CUDA(sc.get(&newlen, (size_t)n + 1));
-    DSG_TRY_CUDA(sc.get(&mid_list, (size_t)n + 1));
-    DSG_TRY_CUDA(sc.get(&big_list, (size_t)n + 1));
     DSG_TRY_CUDA(sc.get(&ctl, 1));
     DSG_TRY_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)n + 1) * 4, s));
     DSG_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IngestCtl), s));
     { LaunchScope ls_("ingest_count_kernel", s); count_kernel<<<grid_for(m_raw, 256), 256, 0, s>>>(n, m_raw, src, dst, cnt, ctl); }
     DSG_TRY_CUDA(cudaGetLastError());
     DSG_TRY_CUDA(device_scan(cnt, n, start, sums, s));
+    { LaunchScope ls_("ingest_classify_count", s); classify_count<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, ctl); }
+    DSG_TRY_CUDA(cudaGetLastError());
     IngestCtl hc;
     uint64_t total = 0;
     DSG_TRY_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -361,21 +560,67 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
         set_error("graph_from_edges: a vertex id is >= n");
         return DSG_EINVAL;
     }
+    ClassLists lists;
+    uint32_t nlist = 0;
+    for (int c = 0; c < kClasses; ++c) {
+        lists.base[c] = nlist;
+        nlist += hc.cls_count[c];
+    }
     DSG_TRY_CUDA(sc.get(&tmp, total ? total : 1));
-    DSG_TRY_CUDA(sc.get(&spare, total ? total : 1));
+    DSG_TRY_CUDA(sc.get(&lists.rows, nlist ? nlist : 1));
     DSG_TRY_CUDA(cudaMemsetAsync(newlen, 0, ((size_t)n + 1) * 4, s));  // reused as the fill counter
     { LaunchScope ls_("ingest_scatter_kernel", s); scatter_kernel<<<grid_for(m_raw, 256), 256, 0, s>>>(n, m_raw, src, dst, start, newlen, tmp); }
     DSG_TRY_CUDA(cudaGetLastError());
     {
         LaunchScope ls_("ingest_sort_small_rows", s);
-        sort_small_rows<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(n, start, cnt, tmp, newlen, mid_list,
-                                                                         big_list, ctl);
+        sort_small_rows<<<grid_for((uint64_t)n, 256), 256, 0, s>>>(n, start, cnt, tmp, newlen, lists, ctl);
     }
     DSG_TRY_CUDA(cudaGetLastError());
-    { LaunchScope ls_("ingest_sort_mid_rows", s); sort_mid_rows<<<dev_info().sms * 4, kMidThreads, 0, s>>>(mid_list, ctl, start, cnt, tmp, newlen); }
+    const uint32_t sms = (uint32_t)dev_info().sms;
+    auto warp_grid = [&](uint32_t rows) { return (uint32_t)std::min<uint64_t>((rows + 7) / 8, (uint64_t)sms * 16); };
+    if (hc.cls_count[0]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<2><<<warp_grid(hc.cls_count[0]), 256, 0, s>>>(lists.rows + lists.base[0], hc.cls_count[0], start, cnt, tmp, newlen); }
+    if (hc.cls_count[1]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<4><<<warp_grid(hc.cls_count[1]), 256, 0, s>>>(lists.rows + lists.base[1], hc.cls_count[1], start, cnt, tmp, newlen); }
+    if (hc.cls_count[2]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<8><<<warp_grid(hc.cls_count[2]), 256, 0, s>>>(lists.rows + lists.base[2], hc.cls_count[2], start, cnt, tmp, newlen); }
+    if (hc.cls_count[3]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<16><<<warp_grid(hc.cls_count[3]), 256, 0, s>>>(lists.rows + lists.base[3], hc.cls_count[3], start, cnt, tmp, newlen); }
+    if (hc.cls_count[4]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<32><<<warp_grid(hc.cls_count[4]), 256, 0, s>>>(lists.rows + lists.base[4], hc.cls_count[4], start, cnt, tmp, newlen); }
     DSG_TRY_CUDA(cudaGetLastError());
-    { LaunchScope ls_("ingest_sort_big_rows", s); sort_big_rows<<<dev_info().sms * 2, kMidThreads, 0, s>>>(big_list, ctl, start, cnt, tmp, spare, newlen); }
+    if (hc.cls_count[5]) {
+        LaunchScope ls_("ingest_sort_block_rows", s);
+        uint32_t g = (uint32_t)std::min<uint64_t>(hc.cls_count[5], (uint64_t)sms * 4);
+        sort_block_rows<<<g, kBlockWarps * 32, 0, s>>>(lists.rows + lists.base[5], hc.cls_count[5], start, cnt, tmp,
+                                                       newlen);
+    }
     DSG_TRY_CUDA(cudaGetLastError());
+    if (hc.cls_count[6]) {
+        const uint32_t ng = hc.cls_count[6];
+        const uint32_t* glist = lists.rows + lists.base[6];
+        const uint32_t nwin = (uint32_t)(((uint64_t)n + kWin - 1) >> kWinBits);
+        const uint64_t pairs = (uint64_t)ng * nwin;
+        uint32_t *hist, *cursor, *ucnt, *spare;
+        uint64_t *hoff, *uoff, *gsums;
+        DSG_TRY_CUDA(sc.get(&spare, total ? total : 1));
+        DSG_TRY_CUDA(sc.get(&hist, pairs));
+        DSG_TRY_CUDA(sc.get(&cursor, pairs));
+        DSG_TRY_CUDA(sc.get(&ucnt, pairs));
+        DSG_TRY_CUDA(sc.get(&hoff, pairs + 1));
+        DSG_TRY_CUDA(sc.get(&uoff, pairs + 1));
+        DSG_TRY_CUDA(sc.get(&gsums, pairs / kScanTile + 2));
+        DSG_TRY_CUDA(cudaMemsetAsync(hist, 0, pairs * 4, s));
+        DSG_TRY_CUDA(cudaMemsetAsync(cursor, 0, pairs * 4, s));
+        dim3 grid(32, std::min<uint32_t>(ng, 65535u));
+        size_t smem = nwin <= 4096 ? (size_t)nwin * 4 : 0;
+        { LaunchScope ls_("ingest_giant_rows", s); giant_hist<<<grid, 256, smem, s>>>(glist, ng, start, cnt, tmp, nwin, hist); }
+        DSG_TRY_CUDA(cudaGetLastError());
+        DSG_TRY_CUDA(device_scan(hist, pairs, hoff, gsums, s));
+        { LaunchScope ls_("ingest_giant_rows", s); giant_scatter<<<grid, 256, 0, s>>>(glist, ng, start, cnt, tmp, nwin, hoff, cursor, spare); }
+        DSG_TRY_CUDA(cudaGetLastError());
+        uint32_t wg = (uint32_t)std::min<uint64_t>((pairs + 7) / 8, (uint64_t)sms * 32);
+        { LaunchScope ls_("ingest_giant_rows", s); giant_windows<false><<<wg, 256, 0, s>>>(glist, ng, start, nwin, hist, hoff, spare, ucnt, nullptr, tmp, newlen); }
+        DSG_TRY_CUDA(cudaGetLastError());
+        DSG_TRY_CUDA(device_scan(ucnt, pairs, uoff, gsums, s));
+        { LaunchScope ls_("ingest_giant_rows", s); giant_windows<true><<<wg, 256, 0, s>>>(glist, ng, start, nwin, hist, hoff, spare, ucnt, uoff, tmp, newlen); }
+        DSG_TRY_CUDA(cudaGetLastError());
+    }
     dsg_graph* g = new dsg_graph();
     g->n = n;
     g->device = dev;

@@ -62,6 +62,7 @@ struct __align__(128) CoreCtl {
     unsigned long long pad7[15];
     unsigned long long levels, subrounds, rem_scanned, rem_written;
     unsigned long long dbg[4];   // bounds-check builds: first bad access (site, index, capacity, level)
+    unsigned long long stamps;
 };
 
 // Bounds checks of the debug build (DSG_DEBUG_BOUNDS): a bad index is
@@ -99,12 +100,27 @@ struct CoreArgs {
     uint64_t limit_ns;
     uint32_t short_max;
     uint32_t chunk_len;
+    uint32_t hot_deg;
+    uint32_t local_max;   // rows up to this length found while draining stay in the block
     uint64_t chunk_cap;
+    uint64_t* trace;      // nullable: block 0 stamps (%globaltimer, kind) after every barrier
+    uint64_t trace_cap;
 };
+
+// Block-local frontier: vertices that reach k while this block drains are
+// drained by the same block in the same sub-round (PKC's thread-local buff,
+// Algorithm 2), so a chain of degree-k vertices costs no grid barrier per
+// link.  Overflow goes to the global frontier of the next sub-round.
+constexpr uint32_t kLocalQ = 1024;
+constexpr uint32_t kLocalWork = 16384;
 
 template <int TB>
 struct CoreSmem {
     TileSmem<TB> tile;
+    AggTable agg;
+    uint32_t lq[kLocalQ];
+    uint32_t lq_tail;
+    uint32_t lq_work;  // row entries this block has taken on locally in this sub-round
     uint64_t bases[4];
     uint64_t red[33];
     uint32_t redm[33];
@@ -137,6 +153,17 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
     CoreCtl* ctl = a.ctl;
     const uint32_t tid = threadIdx.x;
     const uint32_t n = a.n;
+    uint64_t nstamp = 0;
+    // trace entries: 2 words each, (time, kind << 32 | k); kind 0 start, 1 init, 2 scan, 3 drain
+    auto stamp = [&](uint32_t kind, uint32_t kk) {
+        if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 1 < a.trace_cap) {
+            a.trace[2 * nstamp] = global_ns();
+            a.trace[2 * nstamp + 1] = ((uint64_t)kind << 32) | kk;
+        }
+        ++nstamp;
+    };
+    stamp(0, 0);
+    agg_clear(sm.agg);
     // ---- init: deg = row length; least degree -> first level
     {
         uint32_t mn = 0xffffffffu;
@@ -149,6 +176,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         if (tid == 0 && mn != 0xffffffffu) atomicMin(&ctl->next_min[0], mn);
     }
     if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+    stamp(1, 0);
     uint32_t k = ld_relaxed_u32(&ctl->next_min[0]);
     uint64_t rem_n = n, keep_base = 0;
     const uint32_t* rem = nullptr;  // level 0: identity
@@ -191,6 +219,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         uint64_t bp = block_sum<uint64_t>(pushed, sm.red);
         if (tid == 0 && bp) atomicAdd(&ctl->pushedA, (unsigned long long)bp);
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+        stamp(2, k);
         // the level's k has been read by every block: recycle its slot
         if (blockIdx.x == 0 && tid == 0) ctl->next_min[level & 1] = 0xffffffffu;
         // scan-written counters: stable until the next level's scan, which is
@@ -207,28 +236,104 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             uint32_t dmn = 0xffffffffu;
             uint64_t dpushed = 0, natom = 0;
             uint32_t* deg = a.deg;
-            auto visit = [&](uint32_t u, uint32_t v) {
-                DSG_BOUND(ctl, 4, u, n, level, return);
-                if (u == v) return;
-                uint32_t d = deg[u];
-                if (d <= k) return;
-                uint32_t old = atomicSub(&deg[u], 1u);
-                ++natom;
-                if (old == k + 1) {
-                    push_frontier(a, a.Q, &ctl->qtail, a.C, &ctl->ctail, u, a.off[u + 1] - a.off[u]);
-                    ++dpushed;
-                } else if (old <= k) {
-                    atomicAdd(&deg[u], 1u);
-                    ++natom;
-                } else {
-                    dmn = min(dmn, old - 1);
+            // u reached k: drain it in this block if there is room, else globally
+            auto reach_k = [&](uint32_t u) {
+                uint64_t len = a.off[u + 1] - a.off[u];
+                ++dpushed;
+                // keep it in the block while the block's own share stays small:
+                // past kLocalWork entries a grid-wide sub-round is cheaper
+                if (len <= a.local_max && atomicAdd(&sm.lq_work, (uint32_t)len) + len <= kLocalWork) {
+                    uint32_t pos = atomicAdd(&sm.lq_tail, 1u);
+                    if (pos < kLocalQ) {
+                        sm.lq[pos] = u;
+                        return;
+                    }
                 }
+                push_frontier(a, a.Q, &ctl->qtail, a.C, &ctl->ctail, u, len);
             };
+            // c was just taken from u's degree, which was old: keep what brings
+            // it down to k, give back the rest (Algorithm 2's undo, for c units),
+            // and report the crossing into k
+            auto settle = [&](uint32_t u, uint32_t old, uint32_t c) {
+                if (old <= k) {
+                    atomicAdd(&deg[u], c);
+                    ++natom;
+                    return;
+                }
+                uint32_t legit = min(c, old - k);
+                if (legit < c) {
+                    atomicAdd(&deg[u], c - legit);
+                    ++natom;
+                }
+                uint32_t nv = old - legit;
+                if (nv == k) reach_k(u);
+                else dmn = min(dmn, nv);
+            };
+            auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
+                uint32_t d[kBatch], old[kBatch], need = 0;
+#pragma unroll
+                for (uint32_t j = 0; j < kBatch; ++j) {
+                    if (!(valid >> j & 1u)) continue;
+#ifdef DSG_DEBUG_BOUNDS
+                    if (u[j] >= n) {
+                        DSG_BOUND(ctl, 4, u[j], n, level, (void)0);
+                        continue;
+                    }
+#endif
+                    if (u[j] == v[j]) continue;
+                    d[j] = deg[u[j]];
+                    need |= 1u << j;
+                }
+#pragma unroll
+                for (uint32_t j = 0; j < kBatch; ++j) {
+                    if (!(need >> j & 1u)) continue;
+                    if (d[j] <= k || (d[j] >= a.hot_deg && agg_add(sm.agg, u[j]))) {
+                        need &= ~(1u << j);  // already at k, or settled at the flush
+                        continue;
+                    }
+                    old[j] = atomicSub(&deg[u[j]], 1u);
+                    ++natom;
+                }
+#pragma unroll
+                for (uint32_t j = 0; j < kBatch; ++j)
+                    if (need >> j & 1u) settle(u[j], old[j], 1u);
+            };
+            auto flush = [&]() {
+                __syncthreads();
+                for (uint32_t i = tid; i < kAggSlots; i += TB) {
+                    uint32_t key = sm.agg.key[i];
+                    if (key != kAggEmpty) {
+                        uint32_t c = sm.agg.cnt[i];
+                        sm.agg.key[i] = kAggEmpty;
+                        sm.agg.cnt[i] = 0;
+                        uint32_t old = atomicSub(&deg[key], c);
+                        ++natom;
+                        settle(key, old, c);
+                    }
+                }
+                __syncthreads();
+            };
+            if (tid == 0) {
+                sm.lq_tail = 0;
+                sm.lq_work = 0;
+            }
+            __syncthreads();
             if (first)
                 scan_frontier<TB>(a.off, a.adj, a.QA, qa_lo, qa_hi, a.CA, ca_lo, ca_hi, a.chunk_len, sm.tile, visit,
                                   n);
             else
                 scan_frontier<TB>(a.off, a.adj, a.Q, q_lo, q_hi, a.C, c_lo, c_hi, a.chunk_len, sm.tile, visit, n);
+            flush();
+            // drain what this block found, until it finds nothing more
+            for (uint32_t lq_lo = 0;;) {
+                uint32_t lq_hi = min(sm.lq_tail, kLocalQ);
+                __syncthreads();
+                if (lq_lo >= lq_hi) break;
+                scan_frontier<TB, true>(a.off, a.adj, sm.lq, lq_lo, lq_hi, nullptr, 0, 0, a.chunk_len, sm.tile,
+                                        visit, n);
+                flush();
+                lq_lo = lq_hi;
+            }
             uint32_t b2 = block_min_u32(dmn, sm.redm);
             if (tid == 0 && b2 != 0xffffffffu) atomicMin(&ctl->next_min[par_next], b2);
             uint64_t bp2 = block_sum<uint64_t>(dpushed, sm.red);
@@ -236,6 +341,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             uint64_t ba = block_sum<uint64_t>(natom, sm.red);
             if (tid == 0 && ba) atomicAdd(&ctl->atomics, (unsigned long long)ba);
             if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+            stamp(3, k);
             ++subrounds;
             q_lo = q_hi;
             c_lo = c_hi;
@@ -260,6 +366,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         rem_next = (rem_next == a.remA) ? a.remB : a.remA;
     }
     if (blockIdx.x == 0 && tid == 0) {
+        ctl->stamps = nstamp;
         ctl->levels = level;
         ctl->subrounds = subrounds;
         ctl->rem_scanned = rem_scanned;
@@ -277,7 +384,8 @@ static cudaError_t launch_kcore(CoreArgs& a, uint32_t blocks_per_sm, cudaStream_
     return cudaLaunchCooperativeKernel((const void*)kcore_kernel<TB>, dim3(grid), dim3(TB), params, 0, s);
 }
 
-dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats) {
+dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
+                     uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0, uint64_t* stamps = nullptr) {
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
     if (n == 0) return DSG_OK;
@@ -292,6 +400,10 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     a.short_max = tu.short_max;
     a.chunk_len = tu.chunk_len;
     a.chunk_cap = chunk_cap;
+    a.hot_deg = tu.hot_deg;
+    a.local_max = tu.local_max;
+    a.trace = trace_dev;
+    a.trace_cap = trace_cap;
     bool direct = is_device_ptr(core_out);
     if (direct) a.deg = core_out;
     else DSG_TRY_CUDA(sc.get(&a.deg, n));
@@ -320,6 +432,7 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
                   c.dbg[3]);
         return DSG_ECUDA;
     }
+    if (stamps) *stamps = c.stamps;
     const uint64_t vals[5] = {c.levels, c.subrounds, c.rem_scanned, c.rem_written, c.atomics};
     for (uint32_t i = 0; stats && i < nstats && i < 5; ++i) stats[i] = vals[i];
     return status_from_err(c.err, "kcore");
@@ -343,4 +456,26 @@ extern "C" dsg_status dsg_kcore_stats(const dsg_graph* g, uint32_t* out_core, ui
     DSG_CHECK_ARG(out_core || g->n == 0, "out_core is NULL");
     DSG_TRY_CUDA(cudaSetDevice(g->device));
     return run_kcore(g, out_core, stats, nstats);
+}
+
+// Level timestamps of one core decomposition (debug/analysis): pairs
+// (%globaltimer, kind << 32 | k) after every grid barrier; kind 0 = start,
+// 1 = init, 2 = level scan, 3 = drain sub-round.  *count = pairs taken.
+extern "C" dsg_status dsg_debug_kcore_trace(const dsg_graph* g, uint64_t* ts, uint64_t cap, uint64_t* count) {
+    clear_error();
+    DSG_CHECK_ARG(g && ts && cap >= 2, "graph/ts/cap");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    Scratch sc(g->stream);
+    uint64_t* dts;
+    uint32_t* core;
+    DSG_TRY_CUDA(sc.get(&dts, cap));
+    DSG_TRY_CUDA(sc.get(&core, g->n ? g->n : 1));
+    uint64_t stamps = 0;
+    dsg_status st = run_kcore(g, core, nullptr, 0, dts, cap, &stamps);
+    if (st != DSG_OK) return st;
+    uint64_t k = 2 * stamps < cap ? 2 * stamps : cap;
+    DSG_TRY_CUDA(copy_any(ts, dts, k * 8, g->stream));
+    DSG_TRY_CUDA(cudaStreamSynchronize(g->stream));
+    if (count) *count = stamps;
+    return DSG_OK;
 }

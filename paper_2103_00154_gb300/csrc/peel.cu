@@ -43,6 +43,7 @@ struct __align__(128) PeelCtl {
     unsigned long long dec;     // alive-neighbour decrements
     unsigned long long pad7[15];
     unsigned long long rounds, best_round, best_E, best_V;
+    unsigned long long stamps;
 };
 
 struct PeelArgs {
@@ -63,6 +64,9 @@ struct PeelArgs {
     uint64_t limit_ns;
     uint32_t short_max;
     uint32_t chunk_len;
+    uint32_t hot_deg;
+    uint64_t* trace;      // nullable: block 0 stamps %globaltimer after every barrier
+    uint64_t trace_cap;
 };
 
 // floor(2(p+q)E / (qS)) clamped to 32 bits; S > 0.
@@ -76,6 +80,7 @@ __device__ __forceinline__ uint32_t peel_threshold(uint64_t p, uint64_t q, uint6
 template <int TB>
 struct PeelSmem {
     TileSmem<TB> tile;
+    AggTable agg;
     uint64_t bases[4];
     uint64_t red[33];
 };
@@ -91,6 +96,13 @@ __global__ void __launch_bounds__(TB) peel_kernel(PeelArgs a) {
     const uint32_t* alive = nullptr;  // round 0: identity
     uint32_t* next = a.listA;
     uint64_t best_E = E, best_V = S, best_round = 0;
+    uint64_t nstamp = 0;
+    auto stamp = [&]() {
+        if (a.trace && blockIdx.x == 0 && tid == 0 && nstamp < a.trace_cap) a.trace[nstamp] = global_ns();
+        ++nstamp;
+    };
+    stamp();
+    agg_clear(sm.agg);
     if (blockIdx.x == 0 && tid == 0) {
         a.hist_S[0] = S;
         a.hist_E[0] = E;
@@ -148,31 +160,53 @@ __global__ void __launch_bounds__(TB) peel_kernel(PeelArgs a) {
             __syncthreads();
         }
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+        stamp();
         const uint64_t failed_hi = ld_relaxed_u64(&ctl->failed);
         const uint64_t short_hi = ld_relaxed_u64(&ctl->nshort);
         const uint64_t chunk_hi = ld_relaxed_u64(&ctl->nchunk);
         // ------------------------------------------------ phase 2: neighbour scan
         uint64_t dE = 0, ndec = 0;
         uint32_t* st = a.st;
-        auto visit = [&](uint32_t u, uint32_t v) {
+        auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
+            uint32_t w[kBatch];
+#pragma unroll
+            for (uint32_t j = 0; j < kBatch; ++j) {
 #ifdef DSG_DEBUG_BOUNDS
-            if (u >= a.n) { atomicOr(&ctl->err, ERR_RANGE); return; }
+                if ((valid >> j & 1u) && u[j] >= a.n) { atomicOr(&ctl->err, ERR_RANGE); valid &= ~(1u << j); }
 #endif
-            uint32_t w = st[u];
-            if (!(w & kDead)) {
-                atomicSub(&st[u], 1u);
-                ++ndec;
-            } else if (w == mark && u > v) {
-                ++dE;
+                w[j] = (valid >> j & 1u) ? st[u[j]] : kDead;
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kBatch; ++j) {
+                if (!(valid >> j & 1u)) continue;
+                if (!(w[j] & kDead)) {
+                    // w is u's degree at the start of the round (or lower): a
+                    // high one marks a hub, whose decrements are combined per block
+                    if (w[j] < a.hot_deg || !agg_add(sm.agg, u[j])) atomicSub(&st[u[j]], 1u);
+                    ++ndec;
+                } else if (w[j] == mark && u[j] > v[j]) {
+                    ++dE;
+                }
             }
         };
         scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, sm.tile,
                           visit, a.n);
+        // flush the combined hub decrements (block_sum below synchronises first)
+        __syncthreads();
+        for (uint32_t i = tid; i < kAggSlots; i += TB) {
+            uint32_t key = sm.agg.key[i];
+            if (key != kAggEmpty) {
+                atomicSub(&st[key], sm.agg.cnt[i]);
+                sm.agg.key[i] = kAggEmpty;
+                sm.agg.cnt[i] = 0;
+            }
+        }
         uint64_t bdec = block_sum<uint64_t>(ndec, sm.red);
         uint64_t bdE = block_sum<uint64_t>(dE, sm.red) + bdec;
         if (tid == 0 && bdE) atomicAdd(&ctl->dE, (unsigned long long)bdE);
         if (tid == 0 && bdec) atomicAdd(&ctl->dec, (unsigned long long)bdec);
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+        stamp();
         const uint64_t dE_tot = ld_relaxed_u64(&ctl->dE);
         const uint64_t S1 = (uint64_t)a.n - failed_hi;
         const uint64_t E1 = a.m - dE_tot;
@@ -200,6 +234,7 @@ __global__ void __launch_bounds__(TB) peel_kernel(PeelArgs a) {
         if (r >= a.hist_cap) break;
     }
     if (blockIdx.x == 0 && tid == 0) {
+        ctl->stamps = nstamp;
         ctl->rounds = r;
         ctl->best_round = best_round;
         ctl->best_E = best_E;
@@ -231,7 +266,8 @@ static cudaError_t launch_peel(PeelArgs& a, uint32_t blocks_per_sm, cudaStream_t
 // Run the peel; results land in the returned control block and, if given,
 // in hist / peel_round / set (device pointers).
 static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t* hist_S_out, uint64_t* hist_E_out,
-                           uint64_t hist_cap_out, uint32_t* peel_round_out, uint8_t* set_out, PeelCtl* ctl_host) {
+                           uint64_t hist_cap_out, uint32_t* peel_round_out, uint8_t* set_out, PeelCtl* ctl_host,
+                           uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0) {
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
     const Tuning tu = current_tuning();
@@ -257,6 +293,9 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
     a.limit_ns = wait_limit_ns();
     a.short_max = tu.short_max;
     a.chunk_len = tu.chunk_len;
+    a.hot_deg = tu.hot_deg;
+    a.trace = trace_dev;
+    a.trace_cap = trace_cap;
     DSG_TRY_CUDA(sc.get(&a.st, n));
     DSG_TRY_CUDA(sc.get(&a.listA, n));
     DSG_TRY_CUDA(sc.get(&a.listB, n));
@@ -350,6 +389,27 @@ dsg_status dsg_bahmani_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_
                   (unsigned long long)t->hist_cap);
         return DSG_EOVERFLOW;
     }
+    return DSG_OK;
+}
+
+// Phase timestamps of one peel (debug/analysis): ts[i] = %globaltimer after
+// the i-th grid barrier (ts[0] = kernel start).  *count = stamps taken.
+dsg_status dsg_debug_peel_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, uint64_t* ts, uint64_t cap,
+                                uint64_t* count) {
+    clear_error();
+    DSG_CHECK_ARG(g && ts && cap, "graph/ts/cap");
+    DSG_CHECK_ARG(eps_den != 0, "eps_den must be positive");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    Scratch sc(g->stream);
+    uint64_t* dts;
+    DSG_TRY_CUDA(sc.get(&dts, cap));
+    PeelCtl c;
+    dsg_status st = run_peel(g, eps_num, eps_den, nullptr, nullptr, 0, nullptr, nullptr, &c, dts, cap);
+    if (st != DSG_OK) return st;
+    uint64_t k = c.stamps < cap ? c.stamps : cap;
+    DSG_TRY_CUDA(copy_any(ts, dts, k * 8, g->stream));
+    DSG_TRY_CUDA(cudaStreamSynchronize(g->stream));
+    if (count) *count = c.stamps;
     return DSG_OK;
 }
 
@@ -468,6 +528,9 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     a.limit_ns = wait_limit_ns();
     a.short_max = tu.short_max;
     a.chunk_len = tu.chunk_len;
+    a.hot_deg = tu.hot_deg;
+    a.trace = nullptr;
+    a.trace_cap = 0;
     // The buffer keeps whatever the previous call left; only the control
     // block must start at zero (every other array is written before it is read).
     DSG_TRY_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));

@@ -27,6 +27,8 @@ Tuning current_tuning() {
         t.blocks_per_sm = env_u32("DSG_BLOCKS_PER_SM", t.blocks_per_sm);
         t.short_max = env_u32("DSG_SHORT_MAX", t.short_max);
         t.chunk_len = env_u32("DSG_CHUNK_LEN", t.chunk_len);
+        t.hot_deg = env_u32("DSG_HOT_DEG", t.hot_deg);
+        t.local_max = env_u32("DSG_LOCAL_MAX", t.local_max);
         if (t.block != 256 && t.block != 512 && t.block != 1024) t.block = 512;
         if (t.chunk_len < 32) t.chunk_len = 32;
         if (t.short_max < 1) t.short_max = 1;
@@ -51,6 +53,23 @@ extern "C" dsg_status dsg_set_tuning(uint32_t block, uint32_t blocks_per_sm, uin
     g_tune.short_max = short_max;
     g_tune.chunk_len = chunk_len;
     g_tune_set = true;
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_set_hot_degree(uint32_t hot_deg) {
+    clear_error();
+    DSG_CHECK_ARG(hot_deg >= 1, "hot_deg must be positive");
+    current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.hot_deg = hot_deg;
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_set_local_max(uint32_t local_max) {
+    clear_error();
+    current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.local_max = local_max;
     return DSG_OK;
 }
 

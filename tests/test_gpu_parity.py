@@ -144,6 +144,19 @@ def test_rmat_small(scale):
         check_peel(g, c, *pq, tag=f"rmat{scale}")
 
 
+def test_ingest_row_classes_at_scale():
+    # R-MAT scale 17 plus a Chung-Lu graph with 20k-degree hubs: rows land in
+    # every sort class (warp 1/2/4/8/16/32 values per lane, block, and giant
+    # rows split into 16 value windows), with heavy repetition in the hubs
+    for raw in (inputs.rmat(scale=17, m=1 << 21, seed=17),
+                inputs.chung_lu(n=1 << 17, m_draws=1 << 21, gamma=2.1, mean=32.0, wmax=40000.0, seed=3)):
+        c = oracle.from_raw(raw)
+        deg = np.diff(c.off.astype(np.int64))
+        g = gpu_graph(raw)
+        check_csr(g, c, raw.name)
+    assert deg.max() > 8192
+
+
 def test_chung_lu_hubs_cross_every_row_class():
     # hubs of expected degree up to 30000: rows pass 32 (tile/chunk split,
     # warp/block ingest), 256 (several chunks), 4096 and 8192 (merge-path
@@ -198,6 +211,40 @@ def test_results_do_not_depend_on_launch_shape(block, short_max, chunk_len, bps)
     check_core(g, c)
     for pq in [(1, 100), (1, 2)]:
         check_peel(g, c, *pq, tag=f"tune {block}/{short_max}/{chunk_len}/{bps}")
+
+
+@pytest.mark.parametrize("hot_deg", [1, 2, 64, 1 << 30])
+def test_hub_combining_does_not_change_results(hot_deg):
+    # every decrement combined in shared memory (1, 2), hubs only (64), none
+    raw = inputs.chung_lu(n=1 << 14, m_draws=1 << 18, gamma=2.1, mean=32.0, wmax=6000.0, seed=9)
+    c = oracle.from_raw(raw)
+    dsg.set_tuning(hot_deg=hot_deg)
+    g = gpu_graph(raw)
+    check_core(g, c, f"hot {hot_deg}")
+    for pq in [(1, 1000), (1, 10), (0, 1)]:
+        check_peel(g, c, *pq, tag=f"hot {hot_deg}")
+    r2 = inputs.rmat(scale=13, m=1 << 17, seed=21)
+    c2 = oracle.from_raw(r2)
+    g2 = gpu_graph(r2)
+    check_core(g2, c2, f"rmat hot {hot_deg}")
+    check_peel(g2, c2, 1, 10, tag=f"rmat hot {hot_deg}")
+
+
+def test_long_chains_overflow_the_block_queue():
+    # a path of 20000 vertices hanging off a clique: every level-1 vertex joins
+    # a chain far longer than one block's local queue
+    n = 20000 + 40
+    pairs = [(i, i + 1) for i in range(20000 - 1)] + [(20000 + a, 20000 + b) for a in range(40) for b in range(a + 1, 40)]
+    pairs += [(19999, 20000)]
+    raw = inputs.from_pairs(n, pairs)
+    c = oracle.from_raw(raw)
+    for block, local_max in ((256, 1024), (1024, 32), (512, 0), (512, 1 << 30)):
+        dsg.set_tuning(block=block, local_max=local_max)
+        g = gpu_graph(raw)
+        check_core(g, c, f"chain {block}/{local_max}")
+        r2 = inputs.rmat(scale=12, m=1 << 16, seed=5)
+        c2 = oracle.from_raw(r2)
+        check_core(gpu_graph(r2), c2, f"rmat chain {block}/{local_max}")
 
 
 def test_from_csr_paths():
