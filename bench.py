@@ -45,6 +45,11 @@ WORKLOADS = {
              "Bahmani eps=1/10 + core numbers",
         gen=lambda: inputs.er_block(n=10_000, m=50_000, k=100, p=0.5, seed=0),
         eps=[(1, 10)]),
+    "cl22": dict(
+        desc="Chung-Lu n=4,194,304, exponent 2.1, mean degree 32, max expected degree 50,000, seed 2, "
+             "2^26 generated pairs (a quarter-scale config-3 shape for profiling); Bahmani eps=1/10 + core numbers",
+        gen=lambda: inputs.chung_lu(n=1 << 22, m_draws=1 << 26, gamma=2.1, mean=32.0, wmax=5e4, seed=2),
+        eps=[(1, 10)]),
     "cl24": dict(
         desc="Chung-Lu n=16,777,216, exponent 2.1, mean degree 32, max expected degree 100,000, seed 2, "
              "2^28 generated pairs; Bahmani eps=1/10 + core numbers",
@@ -130,6 +135,21 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def aggregate_ranks(total_ms: float, units_per_step: int, steps: int, world: int, device=None):
+    """Replicas only: every rank ran the same workload.  The job's time is the
+    slowest rank's; its throughput counts every rank's units.  Returns
+    (max total_ms over ranks, units/s of the whole job)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = units_per_step * steps * world / (total_ms / 1e3)
+    return total_ms, value
 
 
 # ----------------------------------------------------- byte model (per launch)
@@ -220,14 +240,8 @@ def run_ours(args, wl, raw, rank, world):
     L.dsg_profile_enable(0)
     prof = N.profile_report()
     step_ms = [a.elapsed_time(b) for a, b in events]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
     edges_per_step = 2 * m * (len(wl["eps"]) + 1)
-    value = edges_per_step * args.steps * world / (total_ms / 1e3)
+    total_ms, value = aggregate_ranks(sum(step_ms), edges_per_step, args.steps, world, device=dev)
 
     # roofline of the dominant kernel (largest share of timed device time)
     peak, peak_kind = measured_peaks()

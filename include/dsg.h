@@ -199,15 +199,16 @@ dsg_status dsg_set_tuning(uint32_t block, uint32_t blocks_per_sm, uint32_t short
 dsg_status dsg_get_tuning(uint32_t* block, uint32_t* blocks_per_sm, uint32_t* short_max, uint32_t* chunk_len);
 /* Degree at or above which decrements of a vertex are first combined in a
  * per-block shared-memory table (one global atomic per block and phase for a
- * hub instead of one per edge).  Default 64; DSG_HOT_DEG.  Results never
- * depend on it. */
+ * hub instead of one per edge).  0 (the default) means four times the number
+ * of blocks of the launch; DSG_HOT_DEG.  Results never depend on it. */
 dsg_status dsg_set_hot_degree(uint32_t hot_deg);
 /* Core numbers: a vertex whose row has at most local_max entries and that
  * reaches the current level while a block drains is drained by that block
- * in the same sub-round (PKC's thread-local buffer); longer rows go to the
- * grid-wide frontier.  Default 1024; DSG_LOCAL_MAX.  Results never depend
- * on it. */
-dsg_status dsg_set_local_max(uint32_t local_max);
+ * in the same sub-round (PKC's thread-local buffer), as long as the block's
+ * local entries in that sub-round stay within local_work; other vertices go
+ * to the grid-wide frontier of the next sub-round.  Defaults 1024 / 16384;
+ * DSG_LOCAL_MAX, DSG_LOCAL_WORK.  Results never depend on them. */
+dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work);
 
 /* Upper bound (ns) on every device-side wait (grid barriers, queue polls).
  * A wait that runs out makes its kernel return and the call report
@@ -242,6 +243,10 @@ dsg_status dsg_debug_peel_trace(const dsg_graph* g, uint32_t eps_num, uint32_t e
 dsg_status dsg_debug_kcore_trace(const dsg_graph* g, uint64_t* ts, uint64_t cap, uint64_t* count);
 dsg_status dsg_debug_barrier_ns(uint32_t block, uint32_t blocks_per_sm, uint32_t iters, double* ns,
                                 uint32_t* grid_out);
+/* Throughput (1e9 ops/s) of `ops` random 4-byte accesses to a words-long
+ * device array: mode 0 loads, 1 atomic adds without return, 2 atomic adds
+ * returning the old value (the access patterns of the peel and core kernels). */
+dsg_status dsg_debug_random_access(uint32_t words, uint64_t ops, int mode, double* gops);
 
 /* ------------------------------------------------------- launch accounting */
 

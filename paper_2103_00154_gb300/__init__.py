@@ -32,10 +32,10 @@ def round_bound(n: int, p: int, q: int) -> int:
 
 
 def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, chunk_len: int = 256,
-               hot_deg: int = 64, local_max: int = 1024):
+               hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384):
     N.check(lib().dsg_set_tuning(block, blocks_per_sm, short_max, chunk_len), "set_tuning")
     N.check(lib().dsg_set_hot_degree(hot_deg), "set_hot_degree")
-    N.check(lib().dsg_set_local_max(local_max), "set_local_max")
+    N.check(lib().dsg_set_local_max(local_max, local_work), "set_local_max")
 
 
 def get_tuning():

@@ -57,11 +57,12 @@ _SIGS = [
     ("dsg_set_tuning", c.c_int, [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32]),
     ("dsg_get_tuning", c.c_int, [_U32P, _U32P, _U32P, _U32P]),
     ("dsg_set_hot_degree", c.c_int, [c.c_uint32]),
-    ("dsg_set_local_max", c.c_int, [c.c_uint32]),
+    ("dsg_set_local_max", c.c_int, [c.c_uint32, c.c_uint32]),
     ("dsg_set_wait_limit_ns", None, [c.c_uint64]),
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),
     ("dsg_debug_peel_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, _U64P, c.c_uint64, _U64P]),
     ("dsg_debug_kcore_trace", c.c_int, [_VP, _U64P, c.c_uint64, _U64P]),
+    ("dsg_debug_random_access", c.c_int, [c.c_uint32, c.c_uint64, c.c_int, c.POINTER(c.c_double)]),
     ("dsg_debug_barrier_ns", c.c_int, [c.c_uint32, c.c_uint32, c.c_uint32, c.POINTER(c.c_double), _U32P]),
     ("dsg_launch_count", c.c_ulonglong, []),
     ("dsg_profile_enable", None, [c.c_int]),

@@ -15,8 +15,11 @@ struct Tuning {
     uint32_t blocks_per_sm = 0; // 0: as many as fit
     uint32_t short_max = 32;    // rows up to this length go through the tile path
     uint32_t chunk_len = 256;   // long rows are cut into items of this many entries
-    uint32_t hot_deg = 64;      // decrements of vertices at or above this degree are combined in shared memory
+    uint32_t hot_deg = 0;       // decrements of vertices at or above this degree are combined in shared memory
+                                // (0: four times the number of blocks, i.e. hubs expected to be hit
+                                // several times by every block)
     uint32_t local_max = 1024;  // k-core: rows up to this length reached while draining stay in the block
+    uint32_t local_work = 16384; // k-core: ... while that block's local share of the sub-round stays within this
 };
 
 Tuning current_tuning();
@@ -83,6 +86,12 @@ constexpr uint32_t kAggBits = 11;
 constexpr uint32_t kAggSlots = 1u << kAggBits;
 constexpr uint32_t kAggEmpty = 0xffffffffu;
 
+// The degree at which combining pays: a vertex takes about deg / gridDim.x
+// decrements per block, so combining helps once that is well above one.
+__device__ __forceinline__ uint32_t hot_threshold(uint32_t hot_deg) {
+    return hot_deg ? hot_deg : 4u * gridDim.x;
+}
+
 struct AggTable {
     uint32_t key[kAggSlots];
     uint32_t cnt[kAggSlots];
@@ -110,54 +119,39 @@ __device__ __forceinline__ bool agg_add(AggTable& t, uint32_t u) {
     return false;
 }
 
-// Shared memory of one tile of the row scanner.
+// Shared scratch of the block-wide scans and reductions of the round kernels.
 template <int TB>
 struct TileSmem {
-    uint32_t start[TB];  // exclusive prefix of row lengths
-    uint64_t beg[TB];    // row start in adj
-    uint32_t v[TB];      // row owner
     uint32_t scan_tmp[33];
     uint64_t scan_tmp64[33];
 };
 
-// Walk every adjacency entry of a frontier, handing entries to the visitor
-// four at a time per thread so the visitor can issue four independent loads
-// (then four independent atomics) before it waits on any of them.
-//   short rows: F[lo, hi), one vertex per entry; a block takes TB of them,
-//     prefix-sums their lengths and spreads the concatenated entries evenly
-//     over its threads (consecutive threads read consecutive entries).
-//   long rows: C[clo, chi), items (v << 32 | c) standing for entries
-//     [off[v] + c*chunk_len, min(off[v+1], off[v] + (c+1)*chunk_len)); one warp
-//     per item, 32 consecutive entries per step, four steps in flight.
-// fn(u[4], v[4], valid) is called with bit j of `valid` set for each filled
-// slot j (u = neighbour, v = row owner).
-// LOCAL = true: F is this block's own list (e.g. in shared memory) and only
-// this block walks it; C is ignored.
-constexpr uint32_t kBatch = 4;
+constexpr uint32_t kBatch = 4;  // entries handed to a visitor per thread and call
 
-template <int TB, bool LOCAL = false, class Fn>
-__device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
-                                              const uint32_t* F, uint64_t lo, uint64_t hi,
-                                              const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
-                                              uint32_t chunk_len, TileSmem<TB>& sm, Fn& fn, uint32_t dbg_n = 0) {
+// Shared memory of the block-wide walker below.
+template <int TB>
+struct BlockTile {
+    uint32_t start[TB];  // exclusive prefix of row lengths
+    uint64_t beg[TB];    // row start in adj
+    uint32_t v[TB];      // row owner
+    uint32_t scan_tmp[33];
+};
+
+// Walk the rows of a block-private list F[lo, hi) with the whole block:
+// TB rows at a time, their lengths prefix-summed, the concatenated entries
+// spread evenly over all threads (a few long rows are shared by every warp).
+// Same visitor contract as scan_frontier; every thread of the block calls it.
+template <int TB, class Fn>
+__device__ __forceinline__ void scan_block_list(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
+                                                const uint32_t* F, uint64_t lo, uint64_t hi, BlockTile<TB>& sm,
+                                                Fn& fn) {
     const uint32_t tid = threadIdx.x;
-    const uint64_t t0 = LOCAL ? lo : lo + (uint64_t)blockIdx.x * TB;
-    const uint64_t tstep = LOCAL ? (uint64_t)TB : (uint64_t)gridDim.x * TB;
-    // ---- short rows, edge-balanced inside each tile
-    for (uint64_t t = t0; t < hi; t += tstep) {
-        uint64_t i = t + tid;
+    for (uint64_t t = lo; t < hi; t += TB) {
         uint32_t cnt = (uint32_t)min((uint64_t)TB, hi - t);
         uint32_t v = 0, len = 0;
         uint64_t b = 0;
         if (tid < cnt) {
-            v = F[i];
-#ifdef DSG_DEBUG_BOUNDS
-            if (v >= dbg_n) {
-                uint32_t bu[kBatch] = {0xfffffffeu}, bv[kBatch] = {v};
-                fn(bu, bv, 1u);
-                v = 0;
-            }
-#endif
+            v = F[t + tid];
             b = off[v];
             len = (uint32_t)(off[v + 1] - b);
         }
@@ -175,17 +169,12 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
                 bu[j] = 0;
                 bv[j] = 0;
                 if (e < total) {
-                    // owner = last row whose start is <= e
-                    uint32_t a = 0, z = cnt;
+                    uint32_t a = 0, z = cnt;  // owner = last row whose start is <= e
                     while (z - a > 1) {
                         uint32_t mid = (a + z) >> 1;
                         if (sm.start[mid] <= e) a = mid; else z = mid;
                     }
-                    uint64_t pos = sm.beg[a] + (e - sm.start[a]);
-#ifdef DSG_DEBUG_BOUNDS
-                    if (pos >= off[dbg_n]) { bu[j] = 0xffffffffu; bv[j] = 0xffffffffu; valid |= 1u << j; continue; }
-#endif
-                    bu[j] = adj[pos];
+                    bu[j] = adj[sm.beg[a] + (e - sm.start[a])];
                     bv[j] = sm.v[a];
                     valid |= 1u << j;
                 }
@@ -194,11 +183,84 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
         }
         __syncthreads();
     }
+}
+
+// Walk every adjacency entry of a frontier, handing entries to the visitor
+// four at a time per thread so the visitor can issue four independent loads
+// (then four independent atomics) before it waits on any of them.  No block
+// barrier is used: every warp works on its own share.
+//   short rows: F[lo, hi), one vertex per entry; a warp takes 32 of them,
+//     prefix-sums their lengths with shuffles and spreads the concatenated
+//     entries over its lanes (consecutive lanes read consecutive entries); a
+//     lane finds the row owning an entry by a 5-step shuffle binary search.
+//   long rows: C[clo, chi), items (v << 32 | c) standing for entries
+//     [off[v] + c*chunk_len, min(off[v+1], off[v] + (c+1)*chunk_len)); one warp
+//     per item, 32 consecutive entries per step, four steps in flight.
+// fn(u[4], v[4], valid) is called with bit j of `valid` set for each filled
+// slot j (u = neighbour, v = row owner).  All lanes of a warp call fn
+// together (valid may be 0).
+// LOCAL = true: F is this block's own list (e.g. in shared memory) and only
+// this block's warps walk it; C is ignored.
+template <int TB, bool LOCAL = false, class Fn>
+__device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
+                                              const uint32_t* F, uint64_t lo, uint64_t hi,
+                                              const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
+                                              uint32_t chunk_len, Fn& fn, uint32_t dbg_n = 0) {
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31u;
+    const uint64_t gw = LOCAL ? (uint64_t)(tid >> 5) : ((uint64_t)blockIdx.x * TB + tid) >> 5;
+    const uint64_t nw = LOCAL ? (uint64_t)(TB >> 5) : ((uint64_t)gridDim.x * TB) >> 5;
+    // ---- short rows, 32 per warp, edge-balanced over the warp's lanes
+    for (uint64_t g0 = lo + gw * 32; g0 < hi; g0 += nw * 32) {
+        uint64_t i = g0 + lane;
+        uint32_t v = 0, len = 0;
+        uint64_t b = 0;
+        if (i < hi) {
+            v = F[i];
+#ifdef DSG_DEBUG_BOUNDS
+            if (v >= dbg_n) {
+                uint32_t bu[kBatch] = {0xfffffffeu}, bv[kBatch] = {v};
+                fn(bu, bv, 1u);
+                v = 0;
+            }
+#endif
+            b = off[v];
+            len = (uint32_t)(off[v + 1] - b);
+        }
+        const uint32_t inc = warp_incl_scan(len);
+        const uint32_t total = __shfl_sync(kFullMask, inc, 31);
+        const uint32_t st = inc - len;
+        for (uint32_t e0 = lane; e0 < ((total + 31u) & ~31u); e0 += 32 * kBatch) {
+            uint32_t bu[kBatch], bv[kBatch], valid = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < kBatch; ++j) {
+                const uint32_t e = e0 + 32 * j;
+                // owner = last lane whose start is <= e (all lanes take part in the shuffles)
+                uint32_t a = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1) {
+                    uint32_t s_mid = __shfl_sync(kFullMask, st, a + step);
+                    if (a + step < 32 && s_mid <= e) a += step;
+                }
+                const uint32_t ost = __shfl_sync(kFullMask, st, a);
+                const uint64_t ob = __shfl_sync(kFullMask, b, a);
+                const uint32_t ov = __shfl_sync(kFullMask, v, a);
+                bu[j] = 0;
+                bv[j] = ov;
+                if (e < total) {
+                    uint64_t pos = ob + (e - ost);
+#ifdef DSG_DEBUG_BOUNDS
+                    if (pos >= off[dbg_n]) { bu[j] = 0xffffffffu; bv[j] = 0xffffffffu; valid |= 1u << j; continue; }
+#endif
+                    bu[j] = adj[pos];
+                    valid |= 1u << j;
+                }
+            }
+            fn(bu, bv, valid);
+        }
+    }
     if (LOCAL) return;
     // ---- long rows, one warp per chunk item
-    const uint32_t lane = tid & 31u;
-    const uint64_t gw = ((uint64_t)blockIdx.x * TB + tid) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * TB) >> 5;
     for (uint64_t it = clo + gw; it < chi; it += nw) {
         uint64_t item = C[it];
         uint32_t v = (uint32_t)(item >> 32);

@@ -102,6 +102,7 @@ struct CoreArgs {
     uint32_t chunk_len;
     uint32_t hot_deg;
     uint32_t local_max;   // rows up to this length found while draining stay in the block
+    uint32_t local_work;  // ... while the block's local entries this sub-round stay within this
     uint64_t chunk_cap;
     uint64_t* trace;      // nullable: block 0 stamps (%globaltimer, kind) after every barrier
     uint64_t trace_cap;
@@ -112,11 +113,11 @@ struct CoreArgs {
 // Algorithm 2), so a chain of degree-k vertices costs no grid barrier per
 // link.  Overflow goes to the global frontier of the next sub-round.
 constexpr uint32_t kLocalQ = 1024;
-constexpr uint32_t kLocalWork = 16384;
 
 template <int TB>
 struct CoreSmem {
     TileSmem<TB> tile;
+    BlockTile<TB> btile;
     AggTable agg;
     uint32_t lq[kLocalQ];
     uint32_t lq_tail;
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
     };
     stamp(0, 0);
     agg_clear(sm.agg);
+    const uint32_t hot = hot_threshold(a.hot_deg);
     // ---- init: deg = row length; least degree -> first level
     {
         uint32_t mn = 0xffffffffu;
@@ -241,8 +243,8 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                 uint64_t len = a.off[u + 1] - a.off[u];
                 ++dpushed;
                 // keep it in the block while the block's own share stays small:
-                // past kLocalWork entries a grid-wide sub-round is cheaper
-                if (len <= a.local_max && atomicAdd(&sm.lq_work, (uint32_t)len) + len <= kLocalWork) {
+                // past local_work entries a grid-wide sub-round is cheaper
+                if (len <= a.local_max && atomicAdd(&sm.lq_work, (uint32_t)len) + len <= a.local_work) {
                     uint32_t pos = atomicAdd(&sm.lq_tail, 1u);
                     if (pos < kLocalQ) {
                         sm.lq[pos] = u;
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
 #pragma unroll
                 for (uint32_t j = 0; j < kBatch; ++j) {
                     if (!(need >> j & 1u)) continue;
-                    if (d[j] <= k || (d[j] >= a.hot_deg && agg_add(sm.agg, u[j]))) {
+                    if (d[j] <= k || (d[j] >= hot && agg_add(sm.agg, u[j]))) {
                         need &= ~(1u << j);  // already at k, or settled at the flush
                         continue;
                     }
@@ -319,18 +321,16 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             }
             __syncthreads();
             if (first)
-                scan_frontier<TB>(a.off, a.adj, a.QA, qa_lo, qa_hi, a.CA, ca_lo, ca_hi, a.chunk_len, sm.tile, visit,
-                                  n);
+                scan_frontier<TB>(a.off, a.adj, a.QA, qa_lo, qa_hi, a.CA, ca_lo, ca_hi, a.chunk_len, visit, n);
             else
-                scan_frontier<TB>(a.off, a.adj, a.Q, q_lo, q_hi, a.C, c_lo, c_hi, a.chunk_len, sm.tile, visit, n);
+                scan_frontier<TB>(a.off, a.adj, a.Q, q_lo, q_hi, a.C, c_lo, c_hi, a.chunk_len, visit, n);
             flush();
             // drain what this block found, until it finds nothing more
             for (uint32_t lq_lo = 0;;) {
                 uint32_t lq_hi = min(sm.lq_tail, kLocalQ);
                 __syncthreads();
                 if (lq_lo >= lq_hi) break;
-                scan_frontier<TB, true>(a.off, a.adj, sm.lq, lq_lo, lq_hi, nullptr, 0, 0, a.chunk_len, sm.tile,
-                                        visit, n);
+                scan_block_list<TB>(a.off, a.adj, sm.lq, lq_lo, lq_hi, sm.btile, visit);
                 flush();
                 lq_lo = lq_hi;
             }
@@ -402,6 +402,7 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     a.chunk_cap = chunk_cap;
     a.hot_deg = tu.hot_deg;
     a.local_max = tu.local_max;
+    a.local_work = tu.local_work;
     a.trace = trace_dev;
     a.trace_cap = trace_cap;
     bool direct = is_device_ptr(core_out);

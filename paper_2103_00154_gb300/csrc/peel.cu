@@ -86,7 +86,7 @@ struct PeelSmem {
 };
 
 template <int TB>
-__global__ void __launch_bounds__(TB) peel_kernel(PeelArgs a) {
+__global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a) {
     __shared__ PeelSmem<TB> sm;
     PeelCtl* ctl = a.ctl;
     const uint32_t tid = threadIdx.x;
@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(TB) peel_kernel(PeelArgs a) {
     };
     stamp();
     agg_clear(sm.agg);
+    const uint32_t hot = hot_threshold(a.hot_deg);
     if (blockIdx.x == 0 && tid == 0) {
         a.hist_S[0] = S;
         a.hist_E[0] = E;
@@ -182,15 +183,14 @@ __global__ void __launch_bounds__(TB) peel_kernel(PeelArgs a) {
                 if (!(w[j] & kDead)) {
                     // w is u's degree at the start of the round (or lower): a
                     // high one marks a hub, whose decrements are combined per block
-                    if (w[j] < a.hot_deg || !agg_add(sm.agg, u[j])) atomicSub(&st[u[j]], 1u);
+                    if (w[j] < hot || !agg_add(sm.agg, u[j])) atomicSub(&st[u[j]], 1u);
                     ++ndec;
                 } else if (w[j] == mark && u[j] > v[j]) {
                     ++dE;
                 }
             }
         };
-        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, sm.tile,
-                          visit, a.n);
+        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n);
         // flush the combined hub decrements (block_sum below synchronises first)
         __syncthreads();
         for (uint32_t i = tid; i < kAggSlots; i += TB) {

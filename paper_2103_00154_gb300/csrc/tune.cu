@@ -29,6 +29,7 @@ Tuning current_tuning() {
         t.chunk_len = env_u32("DSG_CHUNK_LEN", t.chunk_len);
         t.hot_deg = env_u32("DSG_HOT_DEG", t.hot_deg);
         t.local_max = env_u32("DSG_LOCAL_MAX", t.local_max);
+        t.local_work = env_u32("DSG_LOCAL_WORK", t.local_work);
         if (t.block != 256 && t.block != 512 && t.block != 1024) t.block = 512;
         if (t.chunk_len < 32) t.chunk_len = 32;
         if (t.short_max < 1) t.short_max = 1;
@@ -58,18 +59,18 @@ extern "C" dsg_status dsg_set_tuning(uint32_t block, uint32_t blocks_per_sm, uin
 
 extern "C" dsg_status dsg_set_hot_degree(uint32_t hot_deg) {
     clear_error();
-    DSG_CHECK_ARG(hot_deg >= 1, "hot_deg must be positive");
     current_tuning();
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.hot_deg = hot_deg;
     return DSG_OK;
 }
 
-extern "C" dsg_status dsg_set_local_max(uint32_t local_max) {
+extern "C" dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work) {
     clear_error();
     current_tuning();
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.local_max = local_max;
+    g_tune.local_work = local_work;
     return DSG_OK;
 }
 

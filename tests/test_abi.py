@@ -61,3 +61,13 @@ def test_argument_errors_are_reported_without_gpu():
     assert L.dsg_kcore(None, None) == N.DSG_EINVAL
     with pytest.raises(dsg.DsgError):
         dsg.set_tuning(block=300)
+
+
+def test_tuning_setters_accept_their_defaults_without_gpu():
+    import paper_2103_00154_gb300 as dsg
+    dsg.set_tuning()
+    t = dsg.get_tuning()
+    assert t["block"] == 512 and t["short_max"] == 32 and t["chunk_len"] == 256
+    dsg.set_tuning(block=1024, blocks_per_sm=1, short_max=8, chunk_len=64, hot_deg=5, local_max=0, local_work=0)
+    assert dsg.get_tuning()["block"] == 1024
+    dsg.set_tuning()
