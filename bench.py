@@ -50,6 +50,12 @@ WORKLOADS = {
              "2^26 generated pairs (a quarter-scale config-3 shape for profiling); Bahmani eps=1/10 + core numbers",
         gen=lambda: inputs.chung_lu(n=1 << 22, m_draws=1 << 26, gamma=2.1, mean=32.0, wmax=5e4, seed=2),
         eps=[(1, 10)]),
+    "batch": dict(
+        desc="4,096 independent graphs (seeds 1000..5095), n log-uniform in [1,000, 1,000,000], even i "
+             "Erdos-Renyi mean degree 8, odd i Chung-Lu exponent 2.3 mean degree 16, each with a planted "
+             "sqrt(n)-vertex block at p=0.3; Bahmani eps=1/10 for every graph, one persistent launch "
+             "(dsg_batch_solve) vs one dsg_bahmani call per graph",
+        kind="batch", eps=[(1, 10)]),
     "cl24": dict(
         desc="Chung-Lu n=16,777,216, exponent 2.1, mean degree 32, max expected degree 100,000, seed 2, "
              "2^28 generated pairs; Bahmani eps=1/10 + core numbers",
@@ -72,6 +78,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in the batch workload")
     return ap.parse_args()
 
 
@@ -319,6 +326,125 @@ def run_e2e(args, wl, raw, dev, edges_per_step, world):
             "d2h_bytes_per_step": d2h, "ms_per_step": dt / steps * 1e3}
 
 
+# ------------------------------------------------------------ batch workload
+def batch_raws(G: int):
+    """Generate the batch members on host threads (the generator releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(lambda i: inputs.batch_graph(i, threads=1), range(G)))
+
+
+def pack_on_device(graphs, dev):
+    """Concatenated CSR of resident graphs, assembled on the device."""
+    import torch
+    import ctypes
+    import paper_2103_00154_gb300 as dsg
+    ns = [g.n for g in graphs]
+    ms = [2 * g.m for g in graphs]
+    G = len(graphs)
+    vb = np.zeros(G + 1, np.uint64)
+    vb[1:] = np.cumsum(ns)
+    ab = np.zeros(G + 1, np.uint64)
+    ab[1:] = np.cumsum(ms)
+    N, A = int(vb[-1]), int(ab[-1])
+    off = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    adj = torch.empty(max(A, 1), dtype=torch.int32, device=dev)
+    L = dsg.lib()
+    for g, gr in enumerate(graphs):
+        o = off[int(vb[g]):int(vb[g]) + gr.n + 1]
+        a = adj[int(ab[g]):int(ab[g]) + 2 * gr.m]
+        tmp = torch.empty(gr.n + 1, dtype=torch.int64, device=dev)
+        dsg._native.check(L.dsg_graph_csr(gr._h, tmp.data_ptr(), a.data_ptr() if gr.m else None), "graph_csr")
+        o.copy_(tmp + int(ab[g]))
+    torch.cuda.synchronize()
+    return torch.from_numpy(vb.view(np.int64)).to(dev), off, adj, N, A
+
+
+def run_batch(args, wl, rank, world):
+    import torch
+    import paper_2103_00154_gb300 as dsg
+    from paper_2103_00154_gb300 import _native as N
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    L = dsg.lib()
+    G = args.batch_graphs
+    t0 = time.perf_counter()
+    raws = batch_raws(G)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    graphs = [dsg.Graph.from_edges(r.n, r.src, r.dst) for r in raws]
+    t_ingest = time.perf_counter() - t0
+    vb, off, adj, Nv, A = pack_on_device(graphs, dev)
+    p, q = wl["eps"][0]
+    solver = dsg.BatchSolver(vb, off, adj, [(p, q)])
+    out_set = torch.empty(max(Nv, 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        E, V, R, BR = solver.solve(out_set=out_set, stream=stream)
+    torch.cuda.synchronize()
+    L.dsg_profile_reset()
+    L.dsg_profile_enable(1)
+    launches0 = L.dsg_launch_count()
+    ms_steps = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            a_ev = torch.cuda.Event(enable_timing=True)
+            b_ev = torch.cuda.Event(enable_timing=True)
+            a_ev.record(stream)
+            E, V, R, BR = solver.solve(out_set=out_set, stream=stream)
+            b_ev.record(stream)
+            b_ev.synchronize()
+            ms_steps.append(a_ev.elapsed_time(b_ev))
+    launches = L.dsg_launch_count() - launches0
+    L.dsg_profile_enable(0)
+    total_ms, value = aggregate_ranks(sum(ms_steps), G, args.steps, world, device=dev)
+    # plain form: one dsg_bahmani per graph on the same resident graphs
+    masks = [torch.empty(max(g.n, 1), dtype=torch.uint8, device=dev) for g in graphs]
+    for g, m in zip(graphs[:64], masks[:64]):
+        g.bahmani(p, q, out_set=m)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [g.bahmani(p, q, out_set=m) for g, m in zip(graphs, masks)]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    same = all((int(E[i]), int(V[i])) == (plain[i][1], plain[i][2]) for i in range(G))
+    return {"ms_per_step": total_ms / args.steps, "value": value, "edges": A, "N": Nv, "t_gen_s": t_gen,
+            "t_ingest_s": t_ingest, "plain_ms": t_plain * 1e3, "plain_graphs_per_s": G / t_plain,
+            "batched_equals_plain": bool(same), "gpu_launches": int(launches), "clocks": clk.summary(),
+            "rounds_max": int(R.max()), "raws": raws, "E": E, "V": V, "R": R, "BR": BR}
+
+
+def batch_cpu_baseline(raws, eps, seconds):
+    """The oracle on whole batch members over all host cores (one graph per
+    process), until about `seconds` have passed; graphs/s of that sample."""
+    import multiprocessing as mproc
+    ctx = mproc.get_context("spawn")
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done, edges = 0, 0
+    with ctx.Pool(cores) as pool:
+        idx = 0
+        while time.perf_counter() - t0 < seconds and idx < len(raws):
+            chunk = raws[idx: idx + cores]
+            idx += len(chunk)
+            for m in pool.starmap(_oracle_one, [(r.n, r.src, r.dst, eps) for r in chunk]):
+                done += 1
+                edges += 2 * m
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "graphs/s", "cores": cores, "kind": "oracle",
+            "edges_per_s": edges / dt,
+            "sample": f"first {done} batch members, one per process on {cores} host cores, {dt:.1f} s"}
+
+
+def _oracle_one(n, src, dst, eps):
+    import oracle
+    c = oracle.canonical_csr(n, src, dst)
+    oracle.bahmani(c, *eps)
+    return c.m
+
+
 # ---------------------------------------------------------------- oracle arm
 def oracle_step(raw, eps):
     import oracle
@@ -384,6 +510,31 @@ def main():
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
+    if wl.get("kind") == "batch":
+        res = run_batch(args, wl, rank, world)
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu:
+            cpu = batch_cpu_baseline(res["raws"], wl["eps"][0], args.cpu_seconds)
+        if rank == 0:
+            print(json.dumps({
+                "metric": "graphs/s", "value": res["value"], "unit": "graphs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": "batch", "desc": wl["desc"], "graphs": args.batch_graphs,
+                           "vertices": res["N"], "adjacency_entries": res["edges"],
+                           "l2": "flushed before every timed step (512 MiB write)"},
+                "edges_scanned_per_s": res["edges"] * args.steps * world / (res["ms_per_step"] * args.steps / 1e3),
+                "plain": {"ms": res["plain_ms"], "graphs_per_s": res["plain_graphs_per_s"],
+                          "form": "one dsg_bahmani call per resident graph, same GPU"},
+                "batched_over_plain": res["value"] / world / res["plain_graphs_per_s"],
+                "batched_equals_plain": res["batched_equals_plain"],
+                "cpu_baseline": cpu, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
+                "host_generation_s": res["t_gen_s"], "ingest_s": res["t_ingest_s"],
+                "rounds_max": res["rounds_max"]}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
     raw = wl["gen"]()
     res = run_ours(args, wl, raw, rank, world)
     cpu = None

@@ -183,6 +183,44 @@ dsg_status dsg_kcore(const dsg_graph* g, uint32_t* out_core);
  *   [4] degree atomics issued (decrements plus undos) */
 dsg_status dsg_kcore_stats(const dsg_graph* g, uint32_t* out_core, uint64_t* stats, uint32_t nstats);
 
+/* ------------------------------------------------------------- batches */
+
+/*
+ * Many independent graphs solved in one launch (the peel of Algorithm 1 for
+ * every graph, core numbers of Algorithm 2's first phase for those asking).
+ * Concatenated CSR: graph g owns vertex slots [vtx_base[g], vtx_base[g+1]);
+ * the row of its local vertex v is adj[off[vtx_base[g]+v] .. off[vtx_base[g]+v+1])
+ * and holds LOCAL neighbour ids (0..n_g-1); each graph's rows are canonical.
+ * Arrays may be host or device memory (host arrays are copied).
+ */
+typedef struct {
+    uint32_t num_graphs;        /* G */
+    const uint64_t* vtx_base;   /* G+1, vtx_base[0] = 0 */
+    const uint64_t* off;        /* vtx_base[G]+1 row offsets into adj */
+    const uint32_t* adj;        /* off[vtx_base[G]] local neighbour ids */
+    const uint32_t* eps_num;    /* G: eps_g = eps_num[g] / eps_den[g] */
+    const uint32_t* eps_den;    /* G, positive */
+    const uint8_t* want_core;   /* G, nullable (NULL: every graph, if result.core is set) */
+} dsg_batch;
+
+typedef struct {
+    uint64_t* E;            /* G, nullable: |E(S~)| per graph (host) */
+    uint64_t* V;            /* G, nullable: |S~| */
+    uint64_t* rounds;       /* G, nullable: R */
+    uint64_t* best_round;   /* G, nullable */
+    uint8_t* out_set;       /* vtx_base[G], nullable: densest-set membership (host or device) */
+    uint32_t* core;         /* vtx_base[G], nullable: core numbers (host or device; untouched
+                               for graphs with want_core[g] == 0) */
+} dsg_batch_result;
+
+/*
+ * Solve a batch in one persistent launch: blocks pull graphs largest first
+ * and each block solves its graph alone (block barriers instead of grid
+ * barriers).  Results equal those of dsg_bahmani / dsg_kcore on each graph
+ * alone.  DSG_EINVAL on malformed offsets or eps_den == 0.
+ */
+dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, void* stream);
+
 /* ------------------------------------------------------------- tuning */
 
 /*

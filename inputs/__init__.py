@@ -66,6 +66,8 @@ def _load():
         lib.gen_chung_lu_weights.restype = ctypes.c_int
         lib.gen_chung_lu_weights.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              _F64P]
+        lib.gen_er_pairs.restype = None
+        lib.gen_er_pairs.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, _U32P, _U32P, ctypes.c_int]
         lib.gen_draw.restype = ctypes.c_uint64
         lib.gen_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
         _lib = lib
@@ -101,6 +103,15 @@ def er(n: int, m: int, seed: int) -> RawGraph:
     return RawGraph(n, src[:got].copy(), dst[:got].copy(), f"er(n={n},m={m},seed={seed})")
 
 
+def er_pairs(n: int, m: int, seed: int, threads: int | None = None) -> RawGraph:
+    """m uniform pairs with replacement (loops and repeats dropped at ingest)."""
+    lib = _load()
+    src = np.empty(max(m, 1), np.uint32)
+    dst = np.empty(max(m, 1), np.uint32)
+    lib.gen_er_pairs(n, m, seed, _p32(src), _p32(dst), threads or _threads())
+    return RawGraph(n, src[:m], dst[:m], f"er_pairs(n={n},m={m},seed={seed})")
+
+
 def block(n: int, k: int, p: float, seed: int) -> RawGraph:
     lib = _load()
     cap = k * (k - 1) // 2 if k > 1 else 1
@@ -133,11 +144,11 @@ def rmat(scale: int = 20, m: int = 1 << 24, a: float = 0.57, b: float = 0.19, c:
 
 
 def chung_lu(n: int = 1 << 24, m_draws: int = 1 << 28, gamma: float = 2.1, mean: float = 32.0,
-             wmax: float = 1e5, seed: int = 2) -> RawGraph:
+             wmax: float = 1e5, seed: int = 2, threads: int | None = None) -> RawGraph:
     lib = _load()
     src = np.empty(max(m_draws, 1), np.uint32)
     dst = np.empty(max(m_draws, 1), np.uint32)
-    if lib.gen_chung_lu(n, m_draws, gamma, mean, wmax, seed, _p32(src), _p32(dst), _threads()) != 0:
+    if lib.gen_chung_lu(n, m_draws, gamma, mean, wmax, seed, _p32(src), _p32(dst), threads or _threads()) != 0:
         raise MemoryError("chung_lu: host allocation failed")
     return RawGraph(n, src[:m_draws], dst[:m_draws], f"chung_lu(n={n},m={m_draws},gamma={gamma},seed={seed})")
 
@@ -149,11 +160,12 @@ def chung_lu_weights(n: int, gamma: float, mean: float, wmax: float) -> np.ndarr
     return w[:n]
 
 
-def batch_graph(i: int, seed_base: int = 1000, n_lo: int = 1_000, n_hi: int = 1_000_000) -> RawGraph:
+def batch_graph(i: int, seed_base: int = 1000, n_lo: int = 1_000, n_hi: int = 1_000_000,
+                threads: int | None = None) -> RawGraph:
     """Member i of the uneven batch: n log-uniform in [n_lo, n_hi]; even i is
-    Erdos-Renyi with mean degree 8, odd i is Chung-Lu (exponent 2.3, mean
-    degree 16, structural cut-off sqrt(16 n)); each gets a planted block of
-    floor(sqrt(n)) vertices at edge probability 0.3."""
+    Erdos-Renyi with mean degree 8 (4n uniform pairs), odd i is Chung-Lu
+    (exponent 2.3, mean degree 16, structural cut-off sqrt(16 n)); each gets a
+    planted block of floor(sqrt(n)) vertices at edge probability 0.3."""
     lib = _load()
     seed = seed_base + i
     u = (lib.gen_draw(seed, 7, 0) >> 11) * 2.0 ** -53
@@ -161,9 +173,9 @@ def batch_graph(i: int, seed_base: int = 1000, n_lo: int = 1_000, n_hi: int = 1_
     n = max(n_lo, min(n_hi, n))
     k = int(math.isqrt(n))
     if i % 2 == 0:
-        base = er(n, 4 * n, seed)
+        base = er_pairs(n, 4 * n, seed, threads)
     else:
-        base = chung_lu(n, 8 * n, 2.3, 16.0, 0.0, seed)
+        base = chung_lu(n, 8 * n, 2.3, 16.0, 0.0, seed, threads)
     g = union(base, block(n, k, 0.3, seed))
     g.name = f"batch[{i}](n={n},{'er' if i % 2 == 0 else 'cl'})"
     return g

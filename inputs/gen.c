@@ -123,6 +123,27 @@ uint64_t gen_er(uint32_t n, uint64_t m, uint64_t seed, uint32_t* src, uint32_t* 
     return got;
 }
 
+/* m pairs drawn uniformly WITH replacement (loops and repeats possible;
+ * ingest drops them).  Threaded. */
+typedef struct {
+    uint32_t n;
+    uint64_t key;
+    uint32_t *src, *dst;
+} erf_ctx;
+
+static void erf_span(void* c, uint64_t lo, uint64_t hi) {
+    erf_ctx* x = (erf_ctx*)c;
+    for (uint64_t i = lo; i < hi; ++i) {
+        x->src[i] = below(draw(x->key, 2 * i), x->n);
+        x->dst[i] = below(draw(x->key, 2 * i + 1), x->n);
+    }
+}
+
+void gen_er_pairs(uint32_t n, uint64_t m, uint64_t seed, uint32_t* src, uint32_t* dst, int threads) {
+    erf_ctx x = {n ? n : 1, stream_key(seed, 6), src, dst};
+    parallel_for(m, threads, erf_span, &x);
+}
+
 /* ------------------------------------------------------- planted block */
 
 /* Block = the first k vertices of a seeded Fisher-Yates permutation of

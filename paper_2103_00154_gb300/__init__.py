@@ -23,7 +23,7 @@ from . import _native as N
 from ._native import (DSG_CSR_CANONICALIZE, DSG_CSR_VALIDATE, DSG_PTRS_DEVICE, DsgError,  # noqa: F401
                       lib)
 
-__all__ = ["Graph", "Trace", "DsgError", "lib", "round_bound", "set_tuning", "get_tuning", "set_wait_limit_ns",
+__all__ = ["Graph", "Trace", "BatchSolver", "pack_batch", "DsgError", "lib", "round_bound", "set_tuning", "get_tuning", "set_wait_limit_ns",
            "DSG_CSR_CANONICALIZE", "DSG_CSR_VALIDATE", "DSG_PTRS_DEVICE"]
 
 
@@ -190,3 +190,58 @@ class Graph:
             out = out[:self.n]
         keys = ("levels", "subrounds", "rem_scanned", "rem_written", "atomics")
         return out, {k: int(v) for k, v in zip(keys, st)}
+
+
+# ------------------------------------------------------------------ batches
+def pack_batch(graphs, device=None):
+    """Concatenated CSR of several graphs (dsg_batch layout): returns
+    (vtx_base, off, adj) as numpy arrays, or torch tensors on `device` when
+    given.  `graphs` are Graph objects or (off, adj) numpy pairs."""
+    offs, adjs = [], []
+    for g in graphs:
+        o, a = g.csr() if isinstance(g, Graph) else g
+        offs.append(np.asarray(o, np.uint64))
+        adjs.append(np.asarray(a, np.uint32))
+    ns = [len(o) - 1 for o in offs]
+    vtx_base = np.zeros(len(graphs) + 1, np.uint64)
+    vtx_base[1:] = np.cumsum(ns)
+    base = 0
+    parts = []
+    for o in offs:
+        parts.append(o[:-1] + np.uint64(base))
+        base += int(o[-1])
+    parts.append(np.array([base], np.uint64))
+    off = np.concatenate(parts) if parts else np.zeros(1, np.uint64)
+    adj = np.concatenate(adjs) if adjs else np.zeros(0, np.uint32)
+    if device is not None:
+        import torch
+        return (torch.from_numpy(vtx_base.view(np.int64)).to(device), torch.from_numpy(off.view(np.int64)).to(device),
+                torch.from_numpy(adj.view(np.int32) if adj.size else np.zeros(1, np.int32)).to(device))
+    return vtx_base, off, adj
+
+
+class BatchSolver:
+    """dsg_batch_solve over a packed batch (see pack_batch)."""
+
+    def __init__(self, vtx_base, off, adj, eps, want_core=None):
+        self.vtx_base, self.off, self.adj = vtx_base, off, adj
+        self.G = int(vtx_base.shape[0]) - 1
+        self.N = int(vtx_base[-1])
+        e = np.asarray(eps, np.uint32).reshape(-1, 2)
+        if e.shape[0] == 1 and self.G > 1:
+            e = np.repeat(e, self.G, axis=0)
+        self.p = np.ascontiguousarray(e[:, 0])
+        self.q = np.ascontiguousarray(e[:, 1])
+        self.want_core = None if want_core is None else np.ascontiguousarray(want_core, np.uint8)
+
+    def solve(self, out_set=None, core=None, stream=None):
+        G = self.G
+        E = np.zeros(max(G, 1), np.uint64)
+        V = np.zeros(max(G, 1), np.uint64)
+        R = np.zeros(max(G, 1), np.uint64)
+        BR = np.zeros(max(G, 1), np.uint64)
+        b = N.Batch(G, N.ptr(self.vtx_base), N.ptr(self.off), N.ptr(self.adj), N.ptr(self.p), N.ptr(self.q),
+                    N.ptr(self.want_core))
+        r = N.BatchResult(N.ptr(E), N.ptr(V), N.ptr(R), N.ptr(BR), N.ptr(out_set), N.ptr(core))
+        N.check(lib().dsg_batch_solve(ctypes.byref(b), ctypes.byref(r), N.stream_handle(stream)), "batch_solve")
+        return E[:G], V[:G], R[:G], BR[:G]

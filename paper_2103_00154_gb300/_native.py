@@ -38,6 +38,15 @@ class Trace(c.Structure):
                 ("peel_round", _VP), ("out_set", _VP), ("edges_scanned", c.c_uint64), ("decrements", c.c_uint64)]
 
 
+class Batch(c.Structure):
+    _fields_ = [("num_graphs", c.c_uint32), ("vtx_base", _VP), ("off", _VP), ("adj", _VP), ("eps_num", _VP),
+                ("eps_den", _VP), ("want_core", _VP)]
+
+
+class BatchResult(c.Structure):
+    _fields_ = [("E", _VP), ("V", _VP), ("rounds", _VP), ("best_round", _VP), ("out_set", _VP), ("core", _VP)]
+
+
 _LIB = None
 
 # (name, restype, argtypes)
@@ -53,6 +62,7 @@ _SIGS = [
     ("dsg_round_bound", c.c_uint64, [c.c_uint32, c.c_uint32, c.c_uint32]),
     ("dsg_bahmani_noalloc", c.c_int, [c.c_uint32, _VP, _VP, c.c_uint32, c.c_uint32, _VP, _U64P, _U64P, _VP]),
     ("dsg_kcore", c.c_int, [_VP, _VP]),
+    ("dsg_batch_solve", c.c_int, [c.POINTER(Batch), c.POINTER(BatchResult), _VP]),
     ("dsg_kcore_stats", c.c_int, [_VP, _VP, _U64P, c.c_uint32]),
     ("dsg_set_tuning", c.c_int, [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32]),
     ("dsg_get_tuning", c.c_int, [_U32P, _U32P, _U32P, _U32P]),

@@ -43,6 +43,15 @@ class LaunchScope {
 dsg_status ingest_from_csr_entries(uint32_t n, const uint64_t* off, const uint32_t* adj, uint64_t total,
                                    uint32_t flags, cudaStream_t s, dsg_graph** out);
 
+// One peel on a graph (any dsg_graph, including a view into a packed batch):
+// set_dev (device, nullable) gets the densest-set mask; out4 = E, V, rounds,
+// best_round.
+dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4]);
+
+// Core numbers of a graph into core_out (host or device); stats nullable.
+dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
+                     uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0, uint64_t* stamps = nullptr);
+
 // Device check that a graph is canonical (sorted rows, no loops, no repeats,
 // symmetric, ids < n).  DSG_EINVAL with a message if not.
 dsg_status validate_csr(const dsg_graph* g);

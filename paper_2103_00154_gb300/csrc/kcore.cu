@@ -385,7 +385,7 @@ static cudaError_t launch_kcore(CoreArgs& a, uint32_t blocks_per_sm, cudaStream_
 }
 
 dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
-                     uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0, uint64_t* stamps = nullptr) {
+                     uint64_t* trace_dev, uint64_t trace_cap, uint64_t* stamps) {
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
     if (n == 0) return DSG_OK;

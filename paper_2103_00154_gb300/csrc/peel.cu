@@ -267,7 +267,22 @@ static cudaError_t launch_peel(PeelArgs& a, uint32_t blocks_per_sm, cudaStream_t
 // in hist / peel_round / set (device pointers).
 static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t* hist_S_out, uint64_t* hist_E_out,
                            uint64_t hist_cap_out, uint32_t* peel_round_out, uint8_t* set_out, PeelCtl* ctl_host,
-                           uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0) {
+                           uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0);
+
+dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4]) {
+    PeelCtl c;
+    dsg_status st = run_peel(g, p, q, nullptr, nullptr, 0, nullptr, set_dev, &c);
+    if (st != DSG_OK) return st;
+    out4[0] = g->n ? c.best_E : 0;
+    out4[1] = g->n ? c.best_V : 0;
+    out4[2] = c.rounds;
+    out4[3] = c.best_round;
+    return DSG_OK;
+}
+
+static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t* hist_S_out, uint64_t* hist_E_out,
+                           uint64_t hist_cap_out, uint32_t* peel_round_out, uint8_t* set_out, PeelCtl* ctl_host,
+                           uint64_t* trace_dev, uint64_t trace_cap) {
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
     const Tuning tu = current_tuning();
