@@ -56,6 +56,11 @@ WORKLOADS = {
              "sqrt(n)-vertex block at p=0.3; Bahmani eps=1/10 for every graph, one persistent launch "
              "(dsg_batch_solve) vs one dsg_bahmani call per graph",
         kind="batch", eps=[(1, 10)]),
+    "serve": dict(
+        desc="Poisson arrivals at 2,000 requests/s (seed 7) over a pool of pre-generated graphs drawn as in the "
+             "batch workload with n log-uniform in [1,000, 2,000,000]; each request asks for Bahmani at eps "
+             "1/100 or 1/10 and, with probability 1/2, core numbers; admitted by free HBM, continuous batching",
+        kind="serve", eps=[(1, 100), (1, 10)]),
     "cl24": dict(
         desc="Chung-Lu n=16,777,216, exponent 2.1, mean degree 32, max expected degree 100,000, seed 2, "
              "2^28 generated pairs; Bahmani eps=1/10 + core numbers",
@@ -79,6 +84,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in the batch workload")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--pool", type=int, default=128, help="serve: distinct pre-generated graphs")
     return ap.parse_args()
 
 
@@ -416,6 +424,102 @@ def run_batch(args, wl, rank, world):
             "rounds_max": int(R.max()), "raws": raws, "E": E, "V": V, "R": R, "BR": BR}
 
 
+def run_serve(args, wl):
+    """Poisson request stream against dsg_serve_*; pool graphs live in pinned
+    host memory and are lent to the server (no copy at submit)."""
+    import threading
+    import torch
+    import paper_2103_00154_gb300 as dsg
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        pool = list(ex.map(lambda i: inputs.batch_graph(i, seed_base=7_000_000, n_hi=2_000_000, threads=1),
+                           range(args.pool)))
+    pinned = [(torch.from_numpy(g.src.view(np.int32)).pin_memory(), torch.from_numpy(g.dst.view(np.int32)).pin_memory())
+              for g in pool]
+    rng = np.random.default_rng(7)
+    n_req = int(args.rate * args.duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req))
+    picks = rng.integers(0, len(pool), n_req)
+    eps_i = rng.integers(0, len(wl["eps"]), n_req)
+    cores = rng.random(n_req) < 0.5
+    # plain form first: one request at a time through the one-graph calls
+    plain_ref = {}
+    t0 = time.perf_counter()
+    n_plain = 0
+    for i in range(min(n_req, 200)):
+        g = pool[picks[i]]
+        p, q = wl["eps"][eps_i[i]]
+        gr = dsg.Graph.from_edges(g.n, pinned[picks[i]][0], pinned[picks[i]][1])
+        _, E, V = gr.bahmani(p, q, want_set=False)
+        if cores[i]:
+            gr.kcore()
+        gr.close()
+        plain_ref[(int(picks[i]), p, q)] = (E, V)
+        n_plain += 1
+    plain_gps = n_plain / (time.perf_counter() - t0)
+    srv = dsg.Server(max_batch=1024)
+    tickets = [None] * n_req
+    rejected = 0
+    done = threading.Event()
+    results = {}
+
+    def collector():
+        i = 0
+        while i < n_req:
+            t = tickets[i]
+            if t is None:
+                if done.is_set() and tickets[i] is None:
+                    i += 1
+                    continue
+                time.sleep(0.0002)
+                continue
+            if t == -1:
+                i += 1
+                continue
+            r = srv.poll(t, 200_000)
+            if r is not None:
+                results[i] = r
+                i += 1
+
+    th = threading.Thread(target=collector)
+    th.start()
+    start = time.perf_counter()
+    for i in range(n_req):
+        delay = start + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        g = pool[picks[i]]
+        p, q = wl["eps"][eps_i[i]]
+        t = srv.submit(g.n, pinned[picks[i]][0], pinned[picks[i]][1], p, q, bool(cores[i]), borrow=True)
+        if t is None:
+            rejected += 1
+            tickets[i] = -1
+        else:
+            tickets[i] = t
+    offered_s = time.perf_counter() - start
+    done.set()
+    th.join()
+    wall = time.perf_counter() - start
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["latency_us"] for r in results.values()])
+    ok = all(r["status"] == 0 for r in results.values())
+    mismatch = 0
+    for i, r in results.items():
+        key = (int(picks[i]), *wl["eps"][eps_i[i]])
+        if key in plain_ref and plain_ref[key] != (r["E"], r["V"]):
+            mismatch += 1
+    completed = len(results)
+    return {"completed": completed, "rejected": rejected, "offered": n_req, "offered_rate": n_req / offered_s,
+            "graphs_per_s": completed / wall, "wall_s": wall, "p50_us": float(np.percentile(lat, 50)) if completed else None,
+            "p99_us": float(np.percentile(lat, 99)) if completed else None, "batches": st["batches"],
+            "plain_graphs_per_s": plain_gps, "all_ok": ok, "mismatch_vs_plain": mismatch,
+            "checked_vs_plain": sum(1 for i in results if (int(picks[i]), *wl["eps"][eps_i[i]]) in plain_ref),
+            "pool": len(pool), "saturated": completed / wall < 0.95 * args.rate}
+
+
 def batch_cpu_baseline(raws, eps, seconds):
     """The oracle on whole batch members over all host cores (one graph per
     process), until about `seconds` have passed; graphs/s of that sample."""
@@ -510,6 +614,22 @@ def main():
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
+    if wl.get("kind") == "serve":
+        res = run_serve(args, wl)
+        if rank == 0:
+            print(json.dumps({
+                "metric": "graphs/s", "value": res["graphs_per_s"], "unit": "graphs/s", "n_gpus": world,
+                "steps": 1, "warmup": 0, "ms_per_step": res["wall_s"] * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": "serve", "desc": wl["desc"], "rate": args.rate, "duration_s": args.duration,
+                           "pool": res["pool"]},
+                "serve": {k: res[k] for k in ("completed", "rejected", "offered", "offered_rate", "p50_us", "p99_us",
+                                              "batches", "saturated", "all_ok", "mismatch_vs_plain",
+                                              "checked_vs_plain")},
+                "plain": {"graphs_per_s": res["plain_graphs_per_s"],
+                          "form": "one request at a time: ingest + dsg_bahmani (+ dsg_kcore) per request"},
+                "served_over_plain": res["graphs_per_s"] / res["plain_graphs_per_s"]}), flush=True)
+        return 0
     if wl.get("kind") == "batch":
         res = run_batch(args, wl, rank, world)
         cpu = None

@@ -221,6 +221,67 @@ typedef struct {
  */
 dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, void* stream);
 
+/* ------------------------------------------------------------- serving */
+
+/*
+ * A serving loop on one GPU: requests (raw pairs + eps) are admitted while
+ * their device-memory charge fits a budget, ingested into resident graphs,
+ * and solved by continuous batching -- whatever was ingested while the
+ * previous batch ran forms the next block-per-graph launch (see
+ * dsg_batch_solve), so arrivals overlap with work already on the device.  A
+ * request's results do not depend on what it is batched with.  All calls
+ * are thread-safe.
+ */
+typedef struct dsg_server dsg_server;
+
+typedef struct {
+    uint32_t max_batch;    /* most graphs per launch (0: 1024) */
+    uint32_t max_pending;  /* queued, not yet admitted requests before DSG_EBUSY (0: 65536) */
+    uint64_t hbm_budget;   /* device bytes admitted requests may hold (0: half the free memory) */
+} dsg_serve_config;
+
+#define DSG_REQ_BORROW 0x1u   /* src/dst stay valid and unchanged until the request completes: no copy */
+
+typedef struct {
+    uint32_t n;              /* vertices 0..n-1 */
+    uint64_t m_raw;          /* raw pairs */
+    const uint32_t* src;     /* host memory, copied by dsg_serve_submit unless DSG_REQ_BORROW */
+    const uint32_t* dst;
+    uint32_t eps_num, eps_den;
+    uint32_t want_core;      /* nonzero: also compute core numbers */
+    uint32_t flags;          /* DSG_REQ_BORROW */
+    uint8_t* out_set;        /* nullable host buffer (n bytes), filled before completion */
+    uint32_t* core;          /* nullable host buffer (n entries), filled when want_core */
+} dsg_request;
+
+typedef struct {
+    dsg_status status;
+    uint32_t n;
+    uint64_t m;              /* undirected edges after ingest */
+    uint64_t E, V, rounds, best_round;
+    double latency_us;       /* submit to completion */
+} dsg_response;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, rejected, pending, in_flight, batches;
+    uint64_t hbm_in_use, hbm_budget;
+    double p50_us, p99_us;   /* latency of completed requests */
+    double graphs_per_s;     /* completed / uptime */
+    double uptime_s;
+} dsg_serve_info;
+
+dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out);
+/* DSG_EBUSY when the queue is full (back-pressure: retry later); DSG_EINVAL
+ * when the request can never fit the budget. */
+dsg_status dsg_serve_submit(dsg_server* s, const dsg_request* r, uint64_t* ticket);
+/* Waits up to timeout_us for the ticket; DSG_EAGAIN if still running,
+ * DSG_ENOTFOUND for an unknown (or already collected) ticket.  A collected
+ * ticket is released. */
+dsg_status dsg_serve_poll(dsg_server* s, uint64_t ticket, dsg_response* resp, uint32_t timeout_us);
+dsg_status dsg_serve_stats(dsg_server* s, dsg_serve_info* out);
+/* Cancels requests not yet admitted, finishes the admitted ones, frees all. */
+void dsg_serve_destroy(dsg_server* s);
+
 /* ------------------------------------------------------------- tuning */
 
 /*

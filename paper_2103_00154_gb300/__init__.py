@@ -23,7 +23,7 @@ from . import _native as N
 from ._native import (DSG_CSR_CANONICALIZE, DSG_CSR_VALIDATE, DSG_PTRS_DEVICE, DsgError,  # noqa: F401
                       lib)
 
-__all__ = ["Graph", "Trace", "BatchSolver", "pack_batch", "DsgError", "lib", "round_bound", "set_tuning", "get_tuning", "set_wait_limit_ns",
+__all__ = ["Graph", "Trace", "BatchSolver", "pack_batch", "Server", "DsgError", "lib", "round_bound", "set_tuning", "get_tuning", "set_wait_limit_ns",
            "DSG_CSR_CANONICALIZE", "DSG_CSR_VALIDATE", "DSG_PTRS_DEVICE"]
 
 
@@ -245,3 +245,76 @@ class BatchSolver:
         r = N.BatchResult(N.ptr(E), N.ptr(V), N.ptr(R), N.ptr(BR), N.ptr(out_set), N.ptr(core))
         N.check(lib().dsg_batch_solve(ctypes.byref(b), ctypes.byref(r), N.stream_handle(stream)), "batch_solve")
         return E[:G], V[:G], R[:G], BR[:G]
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Continuous-batching server (dsg_serve_*).  submit() returns a ticket;
+    poll() returns a dict of the request's results or None while pending."""
+
+    def __init__(self, max_batch: int = 0, max_pending: int = 0, hbm_budget: int = 0):
+        cfg = N.ServeConfig(max_batch, max_pending, hbm_budget)
+        h = ctypes.c_void_p()
+        N.check(lib().dsg_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "serve_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, n, src, dst, p, q, want_core=False, out_set=None, core=None, borrow=False):
+        """Queue a request; None on back-pressure (DSG_EBUSY).  borrow=True:
+        src/dst (host, numpy or pinned torch) are read in place and must stay
+        unchanged until the request completes."""
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, np.uint32)
+            dst = np.ascontiguousarray(dst, np.uint32)
+        m_raw = int(src.shape[0])
+        r = N.Request(n, m_raw, N.ptr(src), N.ptr(dst), p, q, 1 if want_core else 0,
+                      N.DSG_REQ_BORROW if borrow else 0, N.ptr(out_set), N.ptr(core))
+        t = ctypes.c_uint64()
+        st = lib().dsg_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        if st == N.DSG_EBUSY:
+            return None
+        N.check(st, "serve_submit")
+        self._keep[t.value] = (out_set, core, src, dst)
+        return t.value
+
+    def poll(self, ticket, timeout_us: int = 0):
+        resp = N.Response()
+        st = lib().dsg_serve_poll(self._h, ticket, ctypes.byref(resp), timeout_us)
+        if st == N.DSG_EAGAIN:
+            return None
+        N.check(st, "serve_poll")
+        self._keep.pop(ticket, None)
+        return {"status": resp.status, "n": resp.n, "m": resp.m, "E": resp.E, "V": resp.V, "rounds": resp.rounds,
+                "best_round": resp.best_round, "latency_us": resp.latency_us}
+
+    def wait(self, ticket, timeout_s: float = 60.0):
+        import time as _t
+        t_end = _t.monotonic() + timeout_s
+        while True:
+            r = self.poll(ticket, 100_000)
+            if r is not None:
+                return r
+            if _t.monotonic() > t_end:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout_s} s")
+
+    def stats(self):
+        st = N.ServeStats()
+        N.check(lib().dsg_serve_stats(self._h, ctypes.byref(st)), "serve_stats")
+        return {f: getattr(st, f) for f, _ in N.ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dsg_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

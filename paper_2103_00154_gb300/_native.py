@@ -24,6 +24,7 @@ DSG_OK, DSG_EINVAL, DSG_ENOMEM, DSG_ECUDA, DSG_ETIMEOUT, DSG_EBUSY, DSG_EAGAIN, 
 DSG_CSR_CANONICALIZE = 0x1
 DSG_CSR_VALIDATE = 0x2
 DSG_PTRS_DEVICE = 0x4
+DSG_REQ_BORROW = 0x1
 
 
 class DsgError(RuntimeError):
@@ -47,6 +48,29 @@ class BatchResult(c.Structure):
     _fields_ = [("E", _VP), ("V", _VP), ("rounds", _VP), ("best_round", _VP), ("out_set", _VP), ("core", _VP)]
 
 
+class ServeConfig(c.Structure):
+    _fields_ = [("max_batch", c.c_uint32), ("max_pending", c.c_uint32), ("hbm_budget", c.c_uint64)]
+
+
+class Request(c.Structure):
+    _fields_ = [("n", c.c_uint32), ("m_raw", c.c_uint64), ("src", _VP), ("dst", _VP), ("eps_num", c.c_uint32),
+                ("eps_den", c.c_uint32), ("want_core", c.c_uint32), ("flags", c.c_uint32), ("out_set", _VP),
+                ("core", _VP)]
+
+
+class Response(c.Structure):
+    _fields_ = [("status", c.c_int), ("n", c.c_uint32), ("m", c.c_uint64), ("E", c.c_uint64), ("V", c.c_uint64),
+                ("rounds", c.c_uint64), ("best_round", c.c_uint64), ("latency_us", c.c_double)]
+
+
+class ServeStats(c.Structure):
+    _fields_ = [("submitted", c.c_uint64), ("admitted", c.c_uint64), ("completed", c.c_uint64),
+                ("rejected", c.c_uint64), ("pending", c.c_uint64), ("in_flight", c.c_uint64),
+                ("batches", c.c_uint64), ("hbm_in_use", c.c_uint64), ("hbm_budget", c.c_uint64),
+                ("p50_us", c.c_double), ("p99_us", c.c_double), ("graphs_per_s", c.c_double),
+                ("uptime_s", c.c_double)]
+
+
 _LIB = None
 
 # (name, restype, argtypes)
@@ -63,6 +87,11 @@ _SIGS = [
     ("dsg_bahmani_noalloc", c.c_int, [c.c_uint32, _VP, _VP, c.c_uint32, c.c_uint32, _VP, _U64P, _U64P, _VP]),
     ("dsg_kcore", c.c_int, [_VP, _VP]),
     ("dsg_batch_solve", c.c_int, [c.POINTER(Batch), c.POINTER(BatchResult), _VP]),
+    ("dsg_serve_create", c.c_int, [c.POINTER(ServeConfig), c.POINTER(_VP)]),
+    ("dsg_serve_submit", c.c_int, [_VP, c.POINTER(Request), _U64P]),
+    ("dsg_serve_poll", c.c_int, [_VP, c.c_uint64, c.POINTER(Response), c.c_uint32]),
+    ("dsg_serve_stats", c.c_int, [_VP, c.POINTER(ServeStats)]),
+    ("dsg_serve_destroy", None, [_VP]),
     ("dsg_kcore_stats", c.c_int, [_VP, _VP, _U64P, c.c_uint32]),
     ("dsg_set_tuning", c.c_int, [c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint32]),
     ("dsg_get_tuning", c.c_int, [_U32P, _U32P, _U32P, _U32P]),

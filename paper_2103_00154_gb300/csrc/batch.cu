@@ -12,32 +12,13 @@
 #include <algorithm>
 #include <vector>
 
+#include "dsg_batch.cuh"
 #include "dsg_common.cuh"
 #include "dsg_kernels.cuh"
 
 namespace dsg {
 
 constexpr uint32_t kDeadB = 0x80000000u;
-
-struct BatchArgs {
-    uint32_t G;
-    const uint64_t* vbase;
-    const uint64_t* off;
-    const uint32_t* adj;
-    const uint32_t* p;
-    const uint32_t* q;
-    const uint8_t* want_core;
-    const uint32_t* order;  // graph ids, largest first
-    uint32_t* st;           // peel state per vertex slot
-    uint32_t* la;           // scratch lists per vertex slot (x3)
-    uint32_t* lb;
-    uint32_t* lf;
-    uint32_t* core;         // core numbers per vertex slot (nullable)
-    uint8_t* out_set;       // membership in the densest set found (nullable)
-    uint64_t* res;          // 4 per graph: E, V, rounds, best_round
-    unsigned long long* next;
-    uint32_t hot_deg;
-};
 
 template <int TB>
 struct BatchSmem {
@@ -59,9 +40,10 @@ __device__ __forceinline__ uint32_t b_threshold(uint64_t p, uint64_t q, uint64_t
 template <int TB>
 __device__ void peel_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
     const uint32_t tid = threadIdx.x;
-    const uint64_t vb = a.vbase[g];
-    const uint32_t n = (uint32_t)(a.vbase[g + 1] - vb);
-    const uint64_t* off = a.off + vb;
+    const uint64_t vb = a.slot[g];
+    const uint32_t n = a.gn[g];
+    const uint64_t* off = a.goff[g];
+    const uint32_t* adj = a.gadj[g];
     uint32_t* st = a.st + vb;
     uint32_t* alive_a = a.la + vb;
     uint32_t* alive_b = a.lb + vb;
@@ -119,7 +101,7 @@ __device__ void peel_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
                 }
             }
         };
-        scan_block_list<TB>(a.off + vb, a.adj, failed, 0, nf, sm.tile, visit);
+        scan_block_list<TB>(off, adj, failed, 0, nf, sm.tile, visit);
         dE = block_sum<uint64_t>(dE, sm.red.scan_tmp64);
         ++r;
         S -= nf;
@@ -150,9 +132,10 @@ __device__ void peel_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
 template <int TB>
 __device__ void kcore_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
     const uint32_t tid = threadIdx.x;
-    const uint64_t vb = a.vbase[g];
-    const uint32_t n = (uint32_t)(a.vbase[g + 1] - vb);
-    const uint64_t* off = a.off + vb;
+    const uint64_t vb = a.slot[g];
+    const uint32_t n = a.gn[g];
+    const uint64_t* off = a.goff[g];
+    const uint32_t* adj = a.gadj[g];
     uint32_t* deg = a.core + vb;
     uint32_t* rem_a = a.la + vb;
     uint32_t* rem_b = a.lb + vb;
@@ -213,7 +196,7 @@ __device__ void kcore_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
                     else mnext = min(mnext, old[j] - 1);
                 }
             };
-            scan_block_list<TB>(a.off + vb, a.adj, Q, q_lo, q_hi, sm.tile, visit);
+            scan_block_list<TB>(off, adj, Q, q_lo, q_hi, sm.tile, visit);
             q_lo = q_hi;
             q_hi = sm.u32[0];
             __syncthreads();
@@ -242,6 +225,19 @@ __global__ void __launch_bounds__(TB) batch_kernel(BatchArgs a) {
         peel_block<TB>(a, g, sm);
         if (a.core && (!a.want_core || a.want_core[g])) kcore_block<TB>(a, g, sm);
     }
+}
+
+cudaError_t batch_launch(const BatchArgs& a, cudaStream_t s) {
+    constexpr int TB = 512;
+    if (a.G == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TB>, TB, 0);
+    if (e != cudaSuccess) return e;
+    uint32_t slots = (uint32_t)(per_sm > 0 ? per_sm : 1) * (uint32_t)dev_info().sms;
+    uint32_t grid = slots < a.G ? slots : a.G;
+    LaunchScope ls("batch_solve", s);
+    batch_kernel<TB><<<grid, TB, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 // want_core[g] read from host or device memory.
@@ -312,12 +308,41 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
     Scratch sc(s);
     BatchArgs a;
     a.G = G;
-    DSG_TRY_CUDA(to_device(sc, b->vtx_base, G + 1, s, &a.vbase));
-    DSG_TRY_CUDA(to_device(sc, b->off, N + 1, s, &a.off));
-    DSG_TRY_CUDA(to_device(sc, b->adj, total, s, &a.adj));
+    const uint64_t* d_off;
+    const uint32_t* d_adj;
+    DSG_TRY_CUDA(to_device(sc, b->off, N + 1, s, &d_off));
+    DSG_TRY_CUDA(to_device(sc, b->adj, total, s, &d_adj));
     DSG_TRY_CUDA(to_device(sc, b->eps_num, G, s, &a.p));
     DSG_TRY_CUDA(to_device(sc, b->eps_den, G, s, &a.q));
     DSG_TRY_CUDA(to_device(sc, b->want_core, b->want_core ? G : 0, s, &a.want_core));
+    {
+        std::vector<const uint64_t*> hoffp(G);
+        std::vector<const uint32_t*> hadjp(G);
+        std::vector<uint32_t> hn(G);
+        for (uint32_t g = 0; g < G; ++g) {
+            hoffp[g] = d_off + vb[g];
+            hadjp[g] = d_adj;
+            hn[g] = (uint32_t)(vb[g + 1] - vb[g]);
+        }
+        const uint64_t** t_off;
+        const uint32_t** t_adj;
+        uint64_t* t_slot;
+        uint32_t* t_n;
+        DSG_TRY_CUDA(sc.get(&t_off, G));
+        DSG_TRY_CUDA(sc.get(&t_adj, G));
+        DSG_TRY_CUDA(sc.get(&t_slot, G));
+        DSG_TRY_CUDA(sc.get(&t_n, G));
+        DSG_TRY_CUDA(copy_any(t_off, hoffp.data(), G * sizeof(void*), s));
+        DSG_TRY_CUDA(copy_any(t_adj, hadjp.data(), G * sizeof(void*), s));
+        DSG_TRY_CUDA(copy_any(t_slot, vb.data(), G * sizeof(uint64_t), s));
+        DSG_TRY_CUDA(copy_any(t_n, hn.data(), G * sizeof(uint32_t), s));
+        a.goff = t_off;
+        a.gadj = t_adj;
+        a.slot = t_slot;
+        a.gn = t_n;
+        // the tables live in stream-ordered scratch: keep the host vectors alive until the copies ran
+        DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    }
     uint32_t* d_order;
     DSG_TRY_CUDA(sc.get(&d_order, G));
     DSG_TRY_CUDA(copy_any(d_order, order.data(), G * sizeof(uint32_t), s));
@@ -366,8 +391,8 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
         dsg_graph view;
         view.n = (uint32_t)(vb[g + 1] - vb[g]);
         view.m = (hoff_ends[g + 1] - hoff_ends[g]) / 2;
-        view.off = const_cast<uint64_t*>(a.off) + vb[g];
-        view.adj = const_cast<uint32_t*>(a.adj);
+        view.off = const_cast<uint64_t*>(d_off) + vb[g];
+        view.adj = const_cast<uint32_t*>(d_adj);
         view.owns = false;
         DSG_TRY_CUDA(cudaGetDevice(&view.device));
         view.stream = s;

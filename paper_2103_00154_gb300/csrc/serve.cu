@@ -1,0 +1,469 @@
+// Serving loop: requests (raw edge pairs + eps) arrive at any time and are
+// answered by continuous batching on one GPU.
+//
+//   submit  copies the request into host memory the server owns and queues
+//           it (DSG_EBUSY when the queue is full: back-pressure);
+//   worker  (one host thread per server) admits queued requests while their
+//           device-memory charge fits the budget, ingests each on the ingest
+//           stream into a resident graph, and whenever no batch is running
+//           launches one block-per-graph launch over everything ingested so
+//           far on the solve stream; while that batch runs it keeps
+//           admitting and ingesting new arrivals, which form the next batch;
+//           a finished batch's results are copied out, its graphs freed and
+//           their charge returned to the budget;
+//   poll    waits (bounded) for one ticket's completion.
+// A request's results do not depend on what it is batched with: each graph is
+// solved by its own block with its own state.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "dsg_batch.cuh"
+#include "dsg_common.cuh"
+#include "dsg_kernels.cuh"
+
+namespace dsg {
+
+static double now_us() {
+    return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServeReq {
+    uint64_t ticket = 0;
+    uint32_t n = 0;
+    uint64_t m_raw = 0;
+    uint32_t* src = nullptr;  // host copy (freed after ingest) or the caller's borrowed arrays
+    uint32_t* dst = nullptr;
+    bool owned = true;
+    uint32_t p = 0, q = 1;
+    bool want_core = false;
+    uint8_t* out_set = nullptr;  // caller's host buffers
+    uint32_t* core = nullptr;
+    double t_submit = 0, t_done = 0;
+    bool done = false;
+    dsg_status status = DSG_OK;
+    uint64_t res[4] = {0, 0, 0, 0};
+    uint64_t m = 0;
+    dsg_graph* g = nullptr;
+    size_t charge = 0;
+};
+
+}  // namespace dsg
+
+struct dsg_server {
+    dsg_serve_config cfg;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<dsg::ServeReq*> pending;
+    std::vector<dsg::ServeReq*> ready;
+    std::unordered_map<uint64_t, dsg::ServeReq*> by_ticket;
+    uint64_t next_ticket = 1;
+    size_t in_use = 0;
+    bool stop = false;
+    std::thread worker;
+    cudaStream_t s_ingest = nullptr, s_solve = nullptr;
+    // statistics
+    uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, batches = 0;
+    std::vector<double> lat_us;
+    double t0 = 0;
+};
+
+namespace dsg {
+
+// device bytes a request may hold while resident: raw pairs during ingest,
+// ingest temporaries, the CSR and the batch scratch
+static size_t request_charge(uint32_t n, uint64_t m_raw) {
+    return (size_t)m_raw * 8 * 4 + (size_t)n * 64 + 4096;
+}
+
+struct Inflight {
+    std::vector<ServeReq*> reqs;
+    BatchArgs a;
+    uint64_t* d_res = nullptr;
+    uint32_t* d_tables = nullptr;  // one allocation for every table and scratch array
+    size_t tables_bytes = 0;
+    std::vector<uint64_t> slot;
+    uint64_t N = 0;
+    cudaEvent_t done_ev = nullptr;
+};
+
+static void finish_request(dsg_server* s, ServeReq* r, dsg_status st) {
+    r->status = st;
+    r->t_done = now_us();
+    if (r->g) {
+        dsg_graph_free(r->g);
+        r->g = nullptr;
+    }
+    if (r->owned) {
+        free(r->src);
+        free(r->dst);
+    }
+    r->src = r->dst = nullptr;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->in_use -= r->charge;
+    r->done = true;
+    s->completed++;
+    s->lat_us.push_back(r->t_done - r->t_submit);
+    s->cv_done.notify_all();
+}
+
+// Ingest one admitted request on the ingest stream (synchronous for that stream only).
+static void ingest_one(dsg_server* s, ServeReq* r) {
+    dsg_graph* g = nullptr;
+    dsg_status st = dsg_graph_from_edges(r->n, r->m_raw, r->src, r->dst, 0, s->s_ingest, &g);
+    if (r->owned) {
+        free(r->src);
+        free(r->dst);
+    }
+    r->src = r->dst = nullptr;
+    if (st != DSG_OK) {
+        finish_request(s, r, st);
+        return;
+    }
+    r->g = g;
+    r->m = g->m;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->ready.push_back(r);
+}
+
+// Build the tables of one batch and launch it on the solve stream.
+static dsg_status launch_batch(dsg_server* s, Inflight& f) {
+    const uint32_t G = (uint32_t)f.reqs.size();
+    // largest first inside the batch
+    std::stable_sort(f.reqs.begin(), f.reqs.end(), [](ServeReq* x, ServeReq* y) {
+        return 2 * x->m + x->n > 2 * y->m + y->n;
+    });
+    f.slot.resize(G + 1);
+    f.slot[0] = 0;
+    for (uint32_t i = 0; i < G; ++i) f.slot[i + 1] = f.slot[i] + f.reqs[i]->n;
+    f.N = f.slot[G];
+    const uint64_t N = f.N ? f.N : 1;
+    // one allocation: tables + scratch + outputs
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_goff = carve(G * sizeof(void*)), o_gadj = carve(G * sizeof(void*)), o_slot = carve(G * 8),
+                 o_gn = carve(G * 4), o_p = carve(G * 4), o_q = carve(G * 4), o_wc = carve(G), o_order = carve(G * 4),
+                 o_st = carve(N * 4), o_la = carve(N * 4), o_lb = carve(N * 4), o_lf = carve(N * 4),
+                 o_core = carve(N * 4), o_set = carve(N), o_res = carve(4 * (size_t)G * 8), o_next = carve(8);
+    f.tables_bytes = off;
+    DSG_TRY_CUDA(dev_alloc((void**)&f.d_tables, off, s->s_solve));
+    unsigned char* base = reinterpret_cast<unsigned char*>(f.d_tables);
+    std::vector<unsigned char> host(o_st, 0);
+    auto put = [&](size_t o, const void* src, size_t bytes) { memcpy(host.data() + o, src, bytes); };
+    std::vector<const uint64_t*> goff(G);
+    std::vector<const uint32_t*> gadj(G);
+    std::vector<uint32_t> gn(G), gp(G), gq(G), order(G);
+    std::vector<uint8_t> wc(G);
+    for (uint32_t i = 0; i < G; ++i) {
+        ServeReq* r = f.reqs[i];
+        goff[i] = r->g->off;
+        gadj[i] = r->g->adj;
+        gn[i] = r->n;
+        gp[i] = r->p;
+        gq[i] = r->q;
+        wc[i] = r->want_core ? 1 : 0;
+        order[i] = i;
+    }
+    put(o_goff, goff.data(), G * sizeof(void*));
+    put(o_gadj, gadj.data(), G * sizeof(void*));
+    put(o_slot, f.slot.data(), G * 8);
+    put(o_gn, gn.data(), G * 4);
+    put(o_p, gp.data(), G * 4);
+    put(o_q, gq.data(), G * 4);
+    put(o_wc, wc.data(), G);
+    put(o_order, order.data(), G * 4);
+    DSG_TRY_CUDA(cudaMemcpyAsync(base, host.data(), o_st, cudaMemcpyHostToDevice, s->s_solve));
+    DSG_TRY_CUDA(cudaMemsetAsync(base + o_next, 0, 8, s->s_solve));
+    BatchArgs& a = f.a;
+    a.G = G;
+    a.goff = reinterpret_cast<const uint64_t* const*>(base + o_goff);
+    a.gadj = reinterpret_cast<const uint32_t* const*>(base + o_gadj);
+    a.slot = reinterpret_cast<const uint64_t*>(base + o_slot);
+    a.gn = reinterpret_cast<const uint32_t*>(base + o_gn);
+    a.p = reinterpret_cast<const uint32_t*>(base + o_p);
+    a.q = reinterpret_cast<const uint32_t*>(base + o_q);
+    a.want_core = reinterpret_cast<const uint8_t*>(base + o_wc);
+    a.order = reinterpret_cast<const uint32_t*>(base + o_order);
+    a.st = reinterpret_cast<uint32_t*>(base + o_st);
+    a.la = reinterpret_cast<uint32_t*>(base + o_la);
+    a.lb = reinterpret_cast<uint32_t*>(base + o_lb);
+    a.lf = reinterpret_cast<uint32_t*>(base + o_lf);
+    a.core = reinterpret_cast<uint32_t*>(base + o_core);
+    a.out_set = reinterpret_cast<uint8_t*>(base + o_set);
+    a.res = reinterpret_cast<uint64_t*>(base + o_res);
+    a.next = reinterpret_cast<unsigned long long*>(base + o_next);
+    a.hot_deg = 0;
+    f.d_res = a.res;
+    DSG_TRY_CUDA(batch_launch(a, s->s_solve));
+    DSG_TRY_CUDA(cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming));
+    DSG_TRY_CUDA(cudaEventRecord(f.done_ev, s->s_solve));
+    // (the pageable staging vector may go: a host-to-device copy from pageable
+    // memory has consumed its source when cudaMemcpyAsync returns)
+    return DSG_OK;
+}
+
+// Copy a finished batch's results out and release its requests.
+static void complete_batch(dsg_server* s, Inflight& f) {
+    const uint32_t G = (uint32_t)f.reqs.size();
+    std::vector<uint64_t> res(4 * (size_t)G);
+    dsg_status st = DSG_OK;
+    if (cudaMemcpyAsync(res.data(), f.d_res, res.size() * 8, cudaMemcpyDeviceToHost, s->s_solve) != cudaSuccess)
+        st = DSG_ECUDA;
+    for (uint32_t i = 0; i < G && st == DSG_OK; ++i) {
+        ServeReq* r = f.reqs[i];
+        if (r->out_set && r->n &&
+            cudaMemcpyAsync(r->out_set, f.a.out_set + f.slot[i], r->n, cudaMemcpyDeviceToHost, s->s_solve) != cudaSuccess)
+            st = DSG_ECUDA;
+        if (r->core && r->want_core && r->n &&
+            cudaMemcpyAsync(r->core, f.a.core + f.slot[i], (size_t)r->n * 4, cudaMemcpyDeviceToHost, s->s_solve) !=
+                cudaSuccess)
+            st = DSG_ECUDA;
+    }
+    if (cudaStreamSynchronize(s->s_solve) != cudaSuccess) st = DSG_ECUDA;
+    for (uint32_t i = 0; i < G; ++i) {
+        ServeReq* r = f.reqs[i];
+        for (int k = 0; k < 4; ++k) r->res[k] = res[4 * (size_t)i + k];
+        finish_request(s, r, st);
+    }
+    dev_free(f.d_tables, s->s_solve);
+    cudaEventDestroy(f.done_ev);
+    f = Inflight();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->batches++;
+}
+
+static void worker_main(dsg_server* s) {
+    cudaSetDevice(s->device);
+    Inflight fl;
+    bool running = false;
+    for (;;) {
+        std::vector<ServeReq*> admit;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (!running && s->pending.empty() && s->ready.empty()) {
+                if (s->stop) break;
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
+            }
+            // admit in arrival order while the budget allows
+            while (!s->pending.empty()) {
+                ServeReq* r = s->pending.front();
+                if (s->in_use + r->charge > s->cfg.hbm_budget && s->in_use > 0) break;
+                s->pending.pop_front();
+                s->in_use += r->charge;
+                s->admitted++;
+                admit.push_back(r);
+                if (admit.size() >= 64) break;  // keep the batch loop responsive
+            }
+        }
+        for (ServeReq* r : admit) ingest_one(s, r);
+        if (running && cudaEventQuery(fl.done_ev) != cudaErrorNotReady) {
+            complete_batch(s, fl);
+            running = false;
+        }
+        if (!running) {
+            std::vector<ServeReq*> batch;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                size_t take = std::min<size_t>(s->ready.size(), s->cfg.max_batch);
+                batch.assign(s->ready.begin(), s->ready.begin() + take);
+                s->ready.erase(s->ready.begin(), s->ready.begin() + take);
+            }
+            if (!batch.empty()) {
+                fl.reqs = batch;
+                dsg_status st = launch_batch(s, fl);
+                if (st != DSG_OK) {
+                    for (ServeReq* r : fl.reqs) finish_request(s, r, st);
+                    if (fl.d_tables) dev_free(fl.d_tables, s->s_solve);
+                    fl = Inflight();
+                } else {
+                    running = true;
+                }
+            }
+        }
+        if (running && admit.empty()) {
+            // nothing to ingest: wait for the batch (bounded) rather than spin
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->pending.empty()) s->cv_work.wait_for(lk, std::chrono::microseconds(200));
+        }
+    }
+    if (running) complete_batch(s, fl);
+}
+
+}  // namespace dsg
+
+using namespace dsg;
+
+extern "C" {
+
+dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out) {
+    clear_error();
+    DSG_CHECK_ARG(out, "out is NULL");
+    dsg_server* s = new dsg_server();
+    if (cfg) s->cfg = *cfg;
+    else memset(&s->cfg, 0, sizeof(s->cfg));
+    if (!s->cfg.max_batch) s->cfg.max_batch = 1024;
+    if (!s->cfg.max_pending) s->cfg.max_pending = 1u << 16;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess && !s->cfg.hbm_budget) {
+        size_t fr = 0, tot = 0;
+        e = cudaMemGetInfo(&fr, &tot);
+        s->cfg.hbm_budget = fr / 2;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_ingest, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_solve, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        set_error("serve_create: %s", cudaGetErrorString(e));
+        delete s;
+        return DSG_ECUDA;
+    }
+    s->t0 = now_us();
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return DSG_OK;
+}
+
+dsg_status dsg_serve_submit(dsg_server* s, const dsg_request* rq, uint64_t* ticket) {
+    clear_error();
+    DSG_CHECK_ARG(s && rq && ticket, "server / request / ticket is NULL");
+    DSG_CHECK_ARG(rq->eps_den != 0, "eps_den must be positive");
+    DSG_CHECK_ARG(rq->n < 0x80000000u, "n must be below 2^31");
+    DSG_CHECK_ARG(rq->m_raw == 0 || (rq->src && rq->dst), "src/dst is NULL");
+    size_t charge = request_charge(rq->n, rq->m_raw);
+    DSG_CHECK_ARG(charge <= s->cfg.hbm_budget, "request larger than the server's device-memory budget");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) {
+            set_error("serve_submit: server is shutting down");
+            return DSG_EBUSY;
+        }
+        if (s->pending.size() >= s->cfg.max_pending) {
+            s->rejected++;
+            set_error("serve_submit: queue full (%zu pending)", s->pending.size());
+            return DSG_EBUSY;
+        }
+    }
+    ServeReq* r = new ServeReq();
+    r->n = rq->n;
+    r->m_raw = rq->m_raw;
+    r->p = rq->eps_num;
+    r->q = rq->eps_den;
+    r->want_core = rq->want_core != 0;
+    r->out_set = rq->out_set;
+    r->core = rq->core;
+    r->charge = charge;
+    if (rq->flags & DSG_REQ_BORROW) {
+        r->owned = false;
+        r->src = const_cast<uint32_t*>(rq->src);
+        r->dst = const_cast<uint32_t*>(rq->dst);
+    } else if (rq->m_raw) {
+        r->src = (uint32_t*)malloc(rq->m_raw * 4);
+        r->dst = (uint32_t*)malloc(rq->m_raw * 4);
+        if (!r->src || !r->dst) {
+            free(r->src);
+            free(r->dst);
+            delete r;
+            set_error("serve_submit: host allocation failed");
+            return DSG_ENOMEM;
+        }
+        memcpy(r->src, rq->src, rq->m_raw * 4);
+        memcpy(r->dst, rq->dst, rq->m_raw * 4);
+    }
+    r->t_submit = now_us();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r->ticket = s->next_ticket++;
+        s->by_ticket[r->ticket] = r;
+        s->pending.push_back(r);
+        s->submitted++;
+    }
+    s->cv_work.notify_one();
+    *ticket = r->ticket;
+    return DSG_OK;
+}
+
+dsg_status dsg_serve_poll(dsg_server* s, uint64_t ticket, dsg_response* resp, uint32_t timeout_us) {
+    clear_error();
+    DSG_CHECK_ARG(s && resp, "server / response is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->by_ticket.find(ticket);
+    if (it == s->by_ticket.end()) {
+        set_error("serve_poll: unknown ticket %llu", (unsigned long long)ticket);
+        return DSG_ENOTFOUND;
+    }
+    ServeReq* r = it->second;
+    if (!r->done && timeout_us)
+        s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; });
+    if (!r->done) return DSG_EAGAIN;
+    resp->status = r->status;
+    resp->n = r->n;
+    resp->m = r->m;
+    resp->E = r->res[0];
+    resp->V = r->res[1];
+    resp->rounds = r->res[2];
+    resp->best_round = r->res[3];
+    resp->latency_us = r->t_done - r->t_submit;
+    s->by_ticket.erase(it);
+    delete r;
+    return DSG_OK;
+}
+
+dsg_status dsg_serve_stats(dsg_server* s, dsg_serve_info* out) {
+    clear_error();
+    DSG_CHECK_ARG(s && out, "server / stats is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(out, 0, sizeof(*out));
+    out->submitted = s->submitted;
+    out->admitted = s->admitted;
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->pending = s->pending.size();
+    out->in_flight = s->admitted - s->completed;
+    out->hbm_in_use = s->in_use;
+    out->hbm_budget = s->cfg.hbm_budget;
+    out->batches = s->batches;
+    out->uptime_s = (now_us() - s->t0) / 1e6;
+    if (!s->lat_us.empty()) {
+        std::vector<double> v = s->lat_us;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
+        out->p50_us = pct(0.50);
+        out->p99_us = pct(0.99);
+        out->graphs_per_s = out->uptime_s > 0 ? (double)s->completed / out->uptime_s : 0;
+    }
+    return DSG_OK;
+}
+
+void dsg_serve_destroy(dsg_server* s) {
+    if (!s) return;
+    {
+        // requests not yet admitted are cancelled; admitted ones are finished
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->pending.clear();
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& kv : s->by_ticket) {
+        if (kv.second->owned) {
+            free(kv.second->src);
+            free(kv.second->dst);
+        }
+        if (kv.second->g) dsg_graph_free(kv.second->g);
+        delete kv.second;
+    }
+    cudaStreamDestroy(s->s_ingest);
+    cudaStreamDestroy(s->s_solve);
+    delete s;
+}
+
+}  // extern "C"
