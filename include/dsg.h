@@ -238,6 +238,7 @@ typedef struct {
     uint32_t max_batch;    /* most graphs per launch (0: 1024) */
     uint32_t max_pending;  /* queued, not yet admitted requests before DSG_EBUSY (0: 65536) */
     uint64_t hbm_budget;   /* device bytes admitted requests may hold (0: half the free memory) */
+    uint32_t max_inflight; /* batches on the device at once, each on its own stream (0: 4) */
 } dsg_serve_config;
 
 #define DSG_REQ_BORROW 0x1u   /* src/dst stay valid and unchanged until the request completes: no copy */

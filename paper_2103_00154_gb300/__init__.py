@@ -252,8 +252,8 @@ class Server:
     """Continuous-batching server (dsg_serve_*).  submit() returns a ticket;
     poll() returns a dict of the request's results or None while pending."""
 
-    def __init__(self, max_batch: int = 0, max_pending: int = 0, hbm_budget: int = 0):
-        cfg = N.ServeConfig(max_batch, max_pending, hbm_budget)
+    def __init__(self, max_batch: int = 0, max_pending: int = 0, hbm_budget: int = 0, max_inflight: int = 0):
+        cfg = N.ServeConfig(max_batch, max_pending, hbm_budget, max_inflight)
         h = ctypes.c_void_p()
         N.check(lib().dsg_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "serve_create")
         self._h = h

@@ -49,7 +49,8 @@ class BatchResult(c.Structure):
 
 
 class ServeConfig(c.Structure):
-    _fields_ = [("max_batch", c.c_uint32), ("max_pending", c.c_uint32), ("hbm_budget", c.c_uint64)]
+    _fields_ = [("max_batch", c.c_uint32), ("max_pending", c.c_uint32), ("hbm_budget", c.c_uint64),
+                ("max_inflight", c.c_uint32)]
 
 
 class Request(c.Structure):

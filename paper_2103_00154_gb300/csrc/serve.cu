@@ -70,7 +70,8 @@ struct dsg_server {
     size_t in_use = 0;
     bool stop = false;
     std::thread worker;
-    cudaStream_t s_ingest = nullptr, s_solve = nullptr;
+    cudaStream_t s_ingest = nullptr;
+    std::vector<cudaStream_t> s_solve;  // one per batch that may be in flight
     // statistics
     uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, batches = 0;
     std::vector<double> lat_us;
@@ -136,7 +137,7 @@ static void ingest_one(dsg_server* s, ServeReq* r) {
 }
 
 // Build the tables of one batch and launch it on the solve stream.
-static dsg_status launch_batch(dsg_server* s, Inflight& f) {
+static dsg_status launch_batch(dsg_server* s, Inflight& f, cudaStream_t ss) {
     const uint32_t G = (uint32_t)f.reqs.size();
     // largest first inside the batch
     std::stable_sort(f.reqs.begin(), f.reqs.end(), [](ServeReq* x, ServeReq* y) {
@@ -155,7 +156,7 @@ static dsg_status launch_batch(dsg_server* s, Inflight& f) {
                  o_st = carve(N * 4), o_la = carve(N * 4), o_lb = carve(N * 4), o_lf = carve(N * 4),
                  o_core = carve(N * 4), o_set = carve(N), o_res = carve(4 * (size_t)G * 8), o_next = carve(8);
     f.tables_bytes = off;
-    DSG_TRY_CUDA(dev_alloc((void**)&f.d_tables, off, s->s_solve));
+    DSG_TRY_CUDA(dev_alloc((void**)&f.d_tables, off, ss));
     unsigned char* base = reinterpret_cast<unsigned char*>(f.d_tables);
     std::vector<unsigned char> host(o_st, 0);
     auto put = [&](size_t o, const void* src, size_t bytes) { memcpy(host.data() + o, src, bytes); };
@@ -181,8 +182,8 @@ static dsg_status launch_batch(dsg_server* s, Inflight& f) {
     put(o_q, gq.data(), G * 4);
     put(o_wc, wc.data(), G);
     put(o_order, order.data(), G * 4);
-    DSG_TRY_CUDA(cudaMemcpyAsync(base, host.data(), o_st, cudaMemcpyHostToDevice, s->s_solve));
-    DSG_TRY_CUDA(cudaMemsetAsync(base + o_next, 0, 8, s->s_solve));
+    DSG_TRY_CUDA(cudaMemcpyAsync(base, host.data(), o_st, cudaMemcpyHostToDevice, ss));
+    DSG_TRY_CUDA(cudaMemsetAsync(base + o_next, 0, 8, ss));
     BatchArgs& a = f.a;
     a.G = G;
     a.goff = reinterpret_cast<const uint64_t* const*>(base + o_goff);
@@ -203,38 +204,38 @@ static dsg_status launch_batch(dsg_server* s, Inflight& f) {
     a.next = reinterpret_cast<unsigned long long*>(base + o_next);
     a.hot_deg = 0;
     f.d_res = a.res;
-    DSG_TRY_CUDA(batch_launch(a, s->s_solve));
+    DSG_TRY_CUDA(batch_launch(a, ss));
     DSG_TRY_CUDA(cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming));
-    DSG_TRY_CUDA(cudaEventRecord(f.done_ev, s->s_solve));
+    DSG_TRY_CUDA(cudaEventRecord(f.done_ev, ss));
     // (the pageable staging vector may go: a host-to-device copy from pageable
     // memory has consumed its source when cudaMemcpyAsync returns)
     return DSG_OK;
 }
 
 // Copy a finished batch's results out and release its requests.
-static void complete_batch(dsg_server* s, Inflight& f) {
+static void complete_batch(dsg_server* s, Inflight& f, cudaStream_t ss) {
     const uint32_t G = (uint32_t)f.reqs.size();
     std::vector<uint64_t> res(4 * (size_t)G);
     dsg_status st = DSG_OK;
-    if (cudaMemcpyAsync(res.data(), f.d_res, res.size() * 8, cudaMemcpyDeviceToHost, s->s_solve) != cudaSuccess)
+    if (cudaMemcpyAsync(res.data(), f.d_res, res.size() * 8, cudaMemcpyDeviceToHost, ss) != cudaSuccess)
         st = DSG_ECUDA;
     for (uint32_t i = 0; i < G && st == DSG_OK; ++i) {
         ServeReq* r = f.reqs[i];
         if (r->out_set && r->n &&
-            cudaMemcpyAsync(r->out_set, f.a.out_set + f.slot[i], r->n, cudaMemcpyDeviceToHost, s->s_solve) != cudaSuccess)
+            cudaMemcpyAsync(r->out_set, f.a.out_set + f.slot[i], r->n, cudaMemcpyDeviceToHost, ss) != cudaSuccess)
             st = DSG_ECUDA;
         if (r->core && r->want_core && r->n &&
-            cudaMemcpyAsync(r->core, f.a.core + f.slot[i], (size_t)r->n * 4, cudaMemcpyDeviceToHost, s->s_solve) !=
+            cudaMemcpyAsync(r->core, f.a.core + f.slot[i], (size_t)r->n * 4, cudaMemcpyDeviceToHost, ss) !=
                 cudaSuccess)
             st = DSG_ECUDA;
     }
-    if (cudaStreamSynchronize(s->s_solve) != cudaSuccess) st = DSG_ECUDA;
+    if (cudaStreamSynchronize(ss) != cudaSuccess) st = DSG_ECUDA;
     for (uint32_t i = 0; i < G; ++i) {
         ServeReq* r = f.reqs[i];
         for (int k = 0; k < 4; ++k) r->res[k] = res[4 * (size_t)i + k];
         finish_request(s, r, st);
     }
-    dev_free(f.d_tables, s->s_solve);
+    dev_free(f.d_tables, ss);
     cudaEventDestroy(f.done_ev);
     f = Inflight();
     std::lock_guard<std::mutex> lk(s->mu);
@@ -243,13 +244,19 @@ static void complete_batch(dsg_server* s, Inflight& f) {
 
 static void worker_main(dsg_server* s) {
     cudaSetDevice(s->device);
-    Inflight fl;
-    bool running = false;
+    const size_t K = s->s_solve.size();
+    std::vector<Inflight> fl(K);
+    std::vector<bool> running(K, false);
+    auto any_running = [&]() {
+        for (size_t k = 0; k < K; ++k)
+            if (running[k]) return true;
+        return false;
+    };
     for (;;) {
         std::vector<ServeReq*> admit;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (!running && s->pending.empty() && s->ready.empty()) {
+            if (!any_running() && s->pending.empty() && s->ready.empty()) {
                 if (s->stop) break;
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
@@ -262,15 +269,20 @@ static void worker_main(dsg_server* s) {
                 s->in_use += r->charge;
                 s->admitted++;
                 admit.push_back(r);
-                if (admit.size() >= 64) break;  // keep the batch loop responsive
+                if (admit.size() >= 16) break;  // keep batch launches and completions responsive
             }
         }
         for (ServeReq* r : admit) ingest_one(s, r);
-        if (running && cudaEventQuery(fl.done_ev) != cudaErrorNotReady) {
-            complete_batch(s, fl);
-            running = false;
+        // finished batches: results out, memory back
+        for (size_t k = 0; k < K; ++k) {
+            if (running[k] && cudaEventQuery(fl[k].done_ev) != cudaErrorNotReady) {
+                complete_batch(s, fl[k], s->s_solve[k]);
+                running[k] = false;
+            }
         }
-        if (!running) {
+        // continuous batching: whatever is ready goes to a free batch slot now
+        for (size_t k = 0; k < K; ++k) {
+            if (running[k]) continue;
             std::vector<ServeReq*> batch;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
@@ -278,25 +290,25 @@ static void worker_main(dsg_server* s) {
                 batch.assign(s->ready.begin(), s->ready.begin() + take);
                 s->ready.erase(s->ready.begin(), s->ready.begin() + take);
             }
-            if (!batch.empty()) {
-                fl.reqs = batch;
-                dsg_status st = launch_batch(s, fl);
-                if (st != DSG_OK) {
-                    for (ServeReq* r : fl.reqs) finish_request(s, r, st);
-                    if (fl.d_tables) dev_free(fl.d_tables, s->s_solve);
-                    fl = Inflight();
-                } else {
-                    running = true;
-                }
+            if (batch.empty()) break;
+            fl[k].reqs = batch;
+            dsg_status st = launch_batch(s, fl[k], s->s_solve[k]);
+            if (st != DSG_OK) {
+                for (ServeReq* r : fl[k].reqs) finish_request(s, r, st);
+                if (fl[k].d_tables) dev_free(fl[k].d_tables, s->s_solve[k]);
+                fl[k] = Inflight();
+            } else {
+                running[k] = true;
             }
         }
-        if (running && admit.empty()) {
-            // nothing to ingest: wait for the batch (bounded) rather than spin
+        if (any_running() && admit.empty()) {
+            // nothing to ingest: wait a little for arrivals or completions rather than spin
             std::unique_lock<std::mutex> lk(s->mu);
-            if (s->pending.empty()) s->cv_work.wait_for(lk, std::chrono::microseconds(200));
+            if (s->pending.empty()) s->cv_work.wait_for(lk, std::chrono::microseconds(100));
         }
     }
-    if (running) complete_batch(s, fl);
+    for (size_t k = 0; k < K; ++k)
+        if (running[k]) complete_batch(s, fl[k], s->s_solve[k]);
 }
 
 }  // namespace dsg
@@ -313,6 +325,7 @@ dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out) {
     else memset(&s->cfg, 0, sizeof(s->cfg));
     if (!s->cfg.max_batch) s->cfg.max_batch = 1024;
     if (!s->cfg.max_pending) s->cfg.max_pending = 1u << 16;
+    if (!s->cfg.max_inflight) s->cfg.max_inflight = 4;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess && !s->cfg.hbm_budget) {
         size_t fr = 0, tot = 0;
@@ -320,7 +333,9 @@ dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out) {
         s->cfg.hbm_budget = fr / 2;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_ingest, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_solve, cudaStreamNonBlocking);
+    s->s_solve.assign(s->cfg.max_inflight, nullptr);
+    for (uint32_t k = 0; k < s->cfg.max_inflight && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&s->s_solve[k], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         set_error("serve_create: %s", cudaGetErrorString(e));
         delete s;
@@ -462,7 +477,8 @@ void dsg_serve_destroy(dsg_server* s) {
         delete kv.second;
     }
     cudaStreamDestroy(s->s_ingest);
-    cudaStreamDestroy(s->s_solve);
+    for (cudaStream_t st : s->s_solve)
+        if (st) cudaStreamDestroy(st);
     delete s;
 }
 
