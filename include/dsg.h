@@ -310,6 +310,28 @@ dsg_status dsg_set_hot_degree(uint32_t hot_deg);
  * DSG_LOCAL_MAX, DSG_LOCAL_WORK.  Results never depend on them. */
 dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work);
 
+/*
+ * Autotuner.  dsg_autotune times candidate launch parameters for the peel
+ * (what bit 0, at eps_num/eps_den) and/or the core numbers (bit 1) on graph g
+ * by coordinate descent over block size, hub threshold, chunk length and
+ * short-row limit (peel) or block size, hub threshold and the local-drain
+ * limits (core numbers), keeping a change only when it is at least 2%
+ * faster.  The winner is recorded for g's size class (floor log2 n,
+ * floor log2 2m) on this device and used by every later solve of a graph of
+ * that class; *trials gets the number of timed solves.  The table is saved
+ * to DSG_TUNE_FILE (if set) after tuning and loaded from it at first use.
+ * Results never depend on tuning.
+ */
+dsg_status dsg_autotune(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, uint32_t what, uint32_t* trials);
+dsg_status dsg_tune_save(const char* path);
+dsg_status dsg_tune_load(const char* path, uint32_t* entries);
+void dsg_tune_clear(void);
+uint32_t dsg_tune_entries(void);
+/* The launch parameters a solve of kernel 0 (peel) or 1 (core numbers) on g
+ * would use now: out = {block, blocks_per_sm, short_max, chunk_len, hot_deg,
+ * local_max, local_work}. */
+dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[7]);
+
 /* Upper bound (ns) on every device-side wait (grid barriers, queue polls).
  * A wait that runs out makes its kernel return and the call report
  * DSG_ETIMEOUT.  0 restores the default (10 s, or DSG_WAIT_LIMIT_NS). */

@@ -44,6 +44,24 @@ def get_tuning():
     return dict(zip(("block", "blocks_per_sm", "short_max", "chunk_len"), (x.value for x in v)))
 
 
+def tune_save(path: str):
+    N.check(lib().dsg_tune_save(path.encode()), "tune_save")
+
+
+def tune_load(path: str) -> int:
+    k = ctypes.c_uint32()
+    N.check(lib().dsg_tune_load(path.encode(), ctypes.byref(k)), "tune_load")
+    return k.value
+
+
+def tune_clear():
+    lib().dsg_tune_clear()
+
+
+def tune_entries() -> int:
+    return int(lib().dsg_tune_entries())
+
+
 def set_wait_limit_ns(ns: int):
     lib().dsg_set_wait_limit_ns(int(ns))
 
@@ -169,6 +187,21 @@ class Graph:
             out_set = out_set[:self.n]
         return Trace(R, t.best_round, t.best_E, t.best_V, hs[:R + 1].copy(), he[:R + 1].copy(), peel_round,
                      out_set, t.edges_scanned, t.decrements)
+
+    def autotune(self, p: int = 1, q: int = 10, peel: bool = True, kcore: bool = True) -> int:
+        """Pick launch parameters for this graph's size class (dsg_autotune);
+        returns the number of timed solves."""
+        t = ctypes.c_uint32()
+        N.check(lib().dsg_autotune(self._h, p, q, (1 if peel else 0) | (2 if kcore else 0), ctypes.byref(t)),
+                "autotune")
+        return t.value
+
+    def tuning(self, kernel: str = "peel") -> dict:
+        """Launch parameters a solve of `kernel` ("peel" or "kcore") on this graph uses now."""
+        v = (ctypes.c_uint32 * 7)()
+        N.check(lib().dsg_tune_lookup(self._h, 0 if kernel == "peel" else 1, v), "tune_lookup")
+        return dict(zip(("block", "blocks_per_sm", "short_max", "chunk_len", "hot_deg", "local_max", "local_work"),
+                        list(v)))
 
     def kcore(self, out=None):
         """Core numbers (Algorithm 2, first phase)."""

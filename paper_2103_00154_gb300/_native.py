@@ -99,6 +99,12 @@ _SIGS = [
     ("dsg_set_hot_degree", c.c_int, [c.c_uint32]),
     ("dsg_set_local_max", c.c_int, [c.c_uint32, c.c_uint32]),
     ("dsg_set_wait_limit_ns", None, [c.c_uint64]),
+    ("dsg_autotune", c.c_int, [_VP, c.c_uint32, c.c_uint32, c.c_uint32, _U32P]),
+    ("dsg_tune_save", c.c_int, [c.c_char_p]),
+    ("dsg_tune_load", c.c_int, [c.c_char_p, _U32P]),
+    ("dsg_tune_clear", None, []),
+    ("dsg_tune_entries", c.c_uint32, []),
+    ("dsg_tune_lookup", c.c_int, [_VP, c.c_uint32, _U32P]),
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),
     ("dsg_debug_peel_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, _U64P, c.c_uint64, _U64P]),
     ("dsg_debug_kcore_trace", c.c_int, [_VP, _U64P, c.c_uint64, _U64P]),

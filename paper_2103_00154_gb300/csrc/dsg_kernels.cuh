@@ -24,6 +24,10 @@ struct Tuning {
 
 Tuning current_tuning();
 
+// Tuning for a solve of kernel 0 (peel) or 1 (core numbers) on graph g: the
+// autotuned entry of g's size class if there is one, else current_tuning().
+Tuning tuning_for(const dsg_graph* g, int kernel);
+
 // Counts one kernel launch and, when profiling is on, brackets it with CUDA
 // events on its stream.  Construct right before the launch, destroy right
 // after it:  { LaunchScope ls("name", s); kernel<<<...>>>(...); }

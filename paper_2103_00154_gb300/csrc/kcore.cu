@@ -389,7 +389,7 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
     if (n == 0) return DSG_OK;
-    const Tuning tu = current_tuning();
+    const Tuning tu = tuning_for(g, 1);
     const uint64_t chunk_cap = (uint64_t)n + (2 * g->m) / tu.chunk_len + 1;
     Scratch sc(s);
     CoreArgs a;

@@ -285,7 +285,7 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
                            uint64_t* trace_dev, uint64_t trace_cap) {
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
-    const Tuning tu = current_tuning();
+    const Tuning tu = tuning_for(g, 0);
     memset(ctl_host, 0, sizeof(PeelCtl));
     if (n == 0) {
         static const uint64_t zero = 0;

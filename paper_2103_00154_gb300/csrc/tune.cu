@@ -7,6 +7,8 @@
 #include "dsg_common.cuh"
 #include "dsg_kernels.cuh"
 
+extern "C" dsg_status dsg_tune_save(const char* path);
+
 namespace dsg {
 
 static std::mutex g_tune_mu;
@@ -81,5 +83,275 @@ extern "C" dsg_status dsg_get_tuning(uint32_t* block, uint32_t* blocks_per_sm, u
     if (blocks_per_sm) *blocks_per_sm = t.blocks_per_sm;
     if (short_max) *short_max = t.short_max;
     if (chunk_len) *chunk_len = t.chunk_len;
+    return DSG_OK;
+}
+
+// ===================================================================== autotuner
+//
+// Launch parameters are picked per (device, kernel, graph-size class): the
+// class of a graph is (floor(log2 n), floor(log2 2m)).  dsg_autotune times
+// candidate settings on a given graph by coordinate descent (one knob at a
+// time, keeping a change only when it is at least 2% faster) and records the
+// winner for the graph's class; solves on graphs of a tuned class use it.
+// The table can be saved to / loaded from a small JSON file, and is loaded
+// from DSG_TUNE_FILE at first use.
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+
+namespace dsg {
+
+static std::map<std::string, Tuning> g_table;
+static std::map<std::string, double> g_table_ms;
+static bool g_table_loaded = false;
+static thread_local const Tuning* g_forced = nullptr;
+
+static int ilog2(uint64_t x) {
+    int l = 0;
+    while (x > 1) { x >>= 1; ++l; }
+    return l;
+}
+
+static std::string device_key() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+    char buf[320];
+    snprintf(buf, sizeof(buf), "%s/%d", pr.name, pr.multiProcessorCount);
+    return buf;
+}
+
+static std::string class_key(const dsg_graph* g, int kernel) {
+    char buf[400];
+    snprintf(buf, sizeof(buf), "%s|%s|%d:%d", device_key().c_str(), kernel == 0 ? "peel" : "kcore", ilog2(g->n),
+             ilog2(2 * g->m));
+    return buf;
+}
+
+static bool parse_u32(const char* obj, const char* name, uint32_t* out) {
+    char pat[64];
+    snprintf(pat, sizeof(pat), "\"%s\":", name);
+    const char* p = strstr(obj, pat);
+    if (!p) return false;
+    *out = (uint32_t)strtoul(p + strlen(pat), nullptr, 10);
+    return true;
+}
+
+static int load_table_locked(const char* path) {
+    FILE* f = fopen(path, "rb");
+    if (!f) return -1;
+    std::string text;
+    char buf[4096];
+    size_t k;
+    while ((k = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
+    fclose(f);
+    int loaded = 0;
+    size_t pos = 0;
+    while ((pos = text.find("{\"key\": \"", pos)) != std::string::npos) {
+        size_t ks = pos + 9, ke = text.find('"', ks);
+        size_t oe = text.find('}', ke);
+        if (ke == std::string::npos || oe == std::string::npos) break;
+        std::string key = text.substr(ks, ke - ks);
+        std::string obj = text.substr(ke, oe - ke);
+        Tuning t;
+        parse_u32(obj.c_str(), "block", &t.block);
+        parse_u32(obj.c_str(), "blocks_per_sm", &t.blocks_per_sm);
+        parse_u32(obj.c_str(), "short_max", &t.short_max);
+        parse_u32(obj.c_str(), "chunk_len", &t.chunk_len);
+        parse_u32(obj.c_str(), "hot_deg", &t.hot_deg);
+        parse_u32(obj.c_str(), "local_max", &t.local_max);
+        parse_u32(obj.c_str(), "local_work", &t.local_work);
+        if ((t.block == 256 || t.block == 512 || t.block == 1024) && t.chunk_len >= 32 && t.short_max >= 1) {
+            g_table[key] = t;
+            ++loaded;
+        }
+        pos = oe;
+    }
+    return loaded;
+}
+
+static void ensure_table_loaded_locked() {
+    if (g_table_loaded) return;
+    g_table_loaded = true;
+    const char* e = getenv("DSG_TUNE_FILE");
+    if (e && *e) load_table_locked(e);
+}
+
+Tuning tuning_for(const dsg_graph* g, int kernel) {
+    if (g_forced) return *g_forced;
+    Tuning base = current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    ensure_table_loaded_locked();
+    if (g_table.empty()) return base;
+    auto it = g_table.find(class_key(g, kernel));
+    return it == g_table.end() ? base : it->second;
+}
+
+dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
+                     uint64_t* trace_dev, uint64_t trace_cap, uint64_t* stamps);
+dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4]);
+
+// Device time of one solve with tuning t forced (best of `reps`), or a negative
+// value if the solve failed.
+static double time_solve(const dsg_graph* g, int kernel, uint32_t p, uint32_t q, const Tuning& t, uint32_t* core,
+                         int reps) {
+    g_forced = &t;
+    double best = -1;
+    for (int r = 0; r < reps; ++r) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, g->stream);
+        dsg_status st;
+        if (kernel == 0) {
+            uint64_t out4[4];
+            st = peel_into(g, p, q, nullptr, out4);
+        } else {
+            st = run_kcore(g, core, nullptr, 0, nullptr, 0, nullptr);
+        }
+        cudaEventRecord(b, g->stream);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        if (st != DSG_OK) {
+            best = -1;
+            break;
+        }
+        if (best < 0 || ms < best) best = ms;
+    }
+    g_forced = nullptr;
+    return best;
+}
+
+}  // namespace dsg
+
+extern "C" dsg_status dsg_autotune(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, uint32_t what,
+                                   uint32_t* trials_out) {
+    clear_error();
+    DSG_CHECK_ARG(g, "graph is NULL");
+    DSG_CHECK_ARG(eps_den != 0, "eps_den must be positive");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    uint32_t trials = 0;
+    uint32_t* core = nullptr;
+    if (what & 2) DSG_TRY_CUDA(dev_alloc((void**)&core, ((size_t)g->n + 1) * 4, g->stream));
+    for (int kernel = 0; kernel < 2; ++kernel) {
+        if (!(what & (1u << kernel))) continue;
+        Tuning best = tuning_for(g, kernel);
+        double t_best = time_solve(g, kernel, eps_num, eps_den, best, core, 2);
+        ++trials;
+        if (t_best < 0) {
+            if (core) dev_free(core, g->stream);
+            return DSG_ECUDA;
+        }
+        struct Knob {
+            uint32_t Tuning::*field;
+            uint32_t values[4];
+            int count;
+        };
+        const Knob peel_knobs[] = {{&Tuning::block, {256, 512, 1024}, 3},
+                                   {&Tuning::hot_deg, {0, 1024, 4096, 16384}, 4},
+                                   {&Tuning::chunk_len, {128, 256, 1024}, 3},
+                                   {&Tuning::short_max, {16, 32, 64}, 3}};
+        const Knob core_knobs[] = {{&Tuning::block, {256, 512, 1024}, 3},
+                                   {&Tuning::hot_deg, {0, 1024, 4096, 16384}, 4},
+                                   {&Tuning::local_max, {256, 1024, 4096}, 3},
+                                   {&Tuning::local_work, {4096, 16384, 65536}, 3}};
+        const Knob* knobs = kernel == 0 ? peel_knobs : core_knobs;
+        for (int kk = 0; kk < 4; ++kk) {
+            for (int vi = 0; vi < knobs[kk].count; ++vi) {
+                Tuning cand = best;
+                cand.*(knobs[kk].field) = knobs[kk].values[vi];
+                if (cand.*(knobs[kk].field) == best.*(knobs[kk].field)) continue;
+                double t = time_solve(g, kernel, eps_num, eps_den, cand, core, 2);
+                ++trials;
+                if (t >= 0 && t < 0.98 * t_best) {
+                    best = cand;
+                    t_best = t;
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        ensure_table_loaded_locked();
+        std::string key = class_key(g, kernel);
+        g_table[key] = best;
+        g_table_ms[key] = t_best;
+    }
+    if (core) dev_free(core, g->stream);
+    cudaStreamSynchronize(g->stream);
+    if (trials_out) *trials_out = trials;
+    const char* e = getenv("DSG_TUNE_FILE");
+    if (e && *e) dsg_tune_save(e);
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_tune_save(const char* path) {
+    clear_error();
+    DSG_CHECK_ARG(path, "path is NULL");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    ensure_table_loaded_locked();
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) {
+        set_error("tune_save: cannot write %s", path);
+        return DSG_EINVAL;
+    }
+    fprintf(f, "{\"dsg_tuning\": 1, \"entries\": [\n");
+    size_t i = 0;
+    for (auto& kv : g_table) {
+        const Tuning& t = kv.second;
+        auto ms = g_table_ms.find(kv.first);
+        fprintf(f,
+                "  {\"key\": \"%s\", \"block\": %u, \"blocks_per_sm\": %u, \"short_max\": %u, \"chunk_len\": %u, "
+                "\"hot_deg\": %u, \"local_max\": %u, \"local_work\": %u, \"ms\": %.4f}%s\n",
+                kv.first.c_str(), t.block, t.blocks_per_sm, t.short_max, t.chunk_len, t.hot_deg, t.local_max,
+                t.local_work, ms == g_table_ms.end() ? -1.0 : ms->second, ++i < g_table.size() ? "," : "");
+    }
+    fprintf(f, "]}\n");
+    fclose(f);
+    if (rename(tmp.c_str(), path) != 0) {
+        set_error("tune_save: cannot move %s into place", tmp.c_str());
+        return DSG_EINVAL;
+    }
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_tune_load(const char* path, uint32_t* entries) {
+    clear_error();
+    DSG_CHECK_ARG(path, "path is NULL");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_table_loaded = true;
+    int k = load_table_locked(path);
+    if (k < 0) {
+        set_error("tune_load: cannot read %s", path);
+        return DSG_EINVAL;
+    }
+    if (entries) *entries = (uint32_t)k;
+    return DSG_OK;
+}
+
+extern "C" void dsg_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_table.clear();
+    g_table_ms.clear();
+    g_table_loaded = true;
+}
+
+extern "C" uint32_t dsg_tune_entries(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (uint32_t)g_table.size();
+}
+
+extern "C" dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[7]) {
+    clear_error();
+    DSG_CHECK_ARG(g && out, "graph or out is NULL");
+    DSG_CHECK_ARG(kernel <= 1, "kernel must be 0 (peel) or 1 (core numbers)");
+    const Tuning t = tuning_for(g, (int)kernel);
+    const uint32_t v[7] = {t.block, t.blocks_per_sm, t.short_max, t.chunk_len, t.hot_deg, t.local_max, t.local_work};
+    memcpy(out, v, sizeof(v));
     return DSG_OK;
 }

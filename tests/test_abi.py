@@ -71,3 +71,30 @@ def test_tuning_setters_accept_their_defaults_without_gpu():
     dsg.set_tuning(block=1024, blocks_per_sm=1, short_max=8, chunk_len=64, hot_deg=5, local_max=0, local_work=0)
     assert dsg.get_tuning()["block"] == 1024
     dsg.set_tuning()
+
+
+def test_tuning_table_file_round_trip_without_gpu(tmp_path):
+    import paper_2103_00154_gb300 as dsg
+    path = tmp_path / "tune.json"
+    path.write_text('{"dsg_tuning": 1, "entries": [\n'
+                    '  {"key": "dev/152|peel|20:24", "block": 1024, "blocks_per_sm": 0, "short_max": 16, '
+                    '"chunk_len": 128, "hot_deg": 4096, "local_max": 1024, "local_work": 16384, "ms": 1.0},\n'
+                    '  {"key": "dev/152|kcore|20:24", "block": 256, "blocks_per_sm": 0, "short_max": 32, '
+                    '"chunk_len": 256, "hot_deg": 0, "local_max": 256, "local_work": 4096, "ms": 2.0},\n'
+                    '  {"key": "bad", "block": 300, "blocks_per_sm": 0, "short_max": 32, '
+                    '"chunk_len": 256, "hot_deg": 0, "local_max": 256, "local_work": 4096, "ms": 2.0}\n]}\n')
+    try:
+        dsg.tune_clear()
+        assert dsg.tune_entries() == 0
+        assert dsg.tune_load(str(path)) == 2          # the entry with an invalid block size is dropped
+        assert dsg.tune_entries() == 2
+        out = tmp_path / "again.json"
+        dsg.tune_save(str(out))
+        dsg.tune_clear()
+        assert dsg.tune_load(str(out)) == 2
+        text = out.read_text()
+        assert '"block": 1024' in text and '"local_work": 4096' in text and "bad" not in text
+        with pytest.raises(RuntimeError):
+            dsg.tune_load(str(tmp_path / "missing.json"))
+    finally:
+        dsg.tune_clear()
