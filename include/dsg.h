@@ -311,6 +311,46 @@ dsg_status dsg_set_hot_degree(uint32_t hot_deg);
 dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work);
 
 /*
+ * Densest k-core and CBDS-P (Algorithm 2).
+ *
+ * dsg_densest_core: the k-core {v : core(v) >= k} of highest density
+ * |E_k| / |V_k| over all k (Sec. 3.2, the approach of Algorithm 2's first
+ * phase; a 2-approximation of the densest subgraph).  On equal density the
+ * smallest k (the largest core) wins.  res gets k_star, E_core = |E_k*|,
+ * V_core = |V_k*|, and E = E_core, V = V_core, n_legit = 0.
+ *
+ * dsg_cbds: the same, followed by Algorithm 2's second phase, which adds to
+ * the densest core every vertex v outside it whose core number lies strictly
+ * between the core's density and k* and which has more neighbours inside the
+ * core than that density ("legit"); each adds those edges, and the edges
+ * among legit vertices are added once.  res->E = m_e, res->V = m_v (the
+ * augmented subgraph's edges and vertices), res->n_legit = #legit.
+ *
+ *   core     nullable, n core numbers (host or device) to use instead of
+ *            computing them (phase 1); every value must be below n (EINVAL
+ *            otherwise).  The results are defined for whatever values are
+ *            given; only true core numbers give the paper's method.
+ *   out_core nullable, n entries (host or device): the core numbers used.
+ *   out_set  nullable, n bytes (host or device): 1 for the vertices of the
+ *            result (densest core, plus the legit vertices for dsg_cbds).
+ * Densities are compared exactly (128-bit cross-multiplication).  n = 0:
+ * all zeros.  Outputs are untouched on error.
+ */
+typedef struct dsg_cbds_result {
+    uint64_t k_star;  /* densest core's k */
+    uint64_t E_core;  /* |E| of the densest core */
+    uint64_t V_core;  /* |V| of the densest core */
+    uint64_t E;       /* |E| of the result */
+    uint64_t V;       /* |V| of the result */
+    uint64_t n_legit; /* vertices added by the second phase */
+} dsg_cbds_result;
+
+dsg_status dsg_densest_core(const dsg_graph* g, const uint32_t* core, uint32_t* out_core, uint8_t* out_set,
+                            dsg_cbds_result* res);
+dsg_status dsg_cbds(const dsg_graph* g, const uint32_t* core, uint32_t* out_core, uint8_t* out_set,
+                    dsg_cbds_result* res);
+
+/*
  * Autotuner.  dsg_autotune times candidate launch parameters for the peel
  * (what bit 0, at eps_num/eps_den) and/or the core numbers (bit 1) on graph g
  * by coordinate descent over block size, hub threshold, chunk length and

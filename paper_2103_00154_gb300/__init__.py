@@ -80,6 +80,21 @@ class Trace:
     decrements: int
 
 
+@dataclass
+class Cbds:
+    """Densest core (k_star, E_core, V_core) and the result (E, V) with its set;
+    for dsg_cbds the result is the densest core grown by Algorithm 2's second
+    phase (n_legit vertices added), for dsg_densest_core it is the core itself."""
+    k_star: int
+    E_core: int
+    V_core: int
+    E: int
+    V: int
+    n_legit: int
+    mask: object
+    core: object
+
+
 def _u32(x):
     if isinstance(x, np.ndarray):
         return np.ascontiguousarray(x, np.uint32)
@@ -195,6 +210,30 @@ class Graph:
         N.check(lib().dsg_autotune(self._h, p, q, (1 if peel else 0) | (2 if kcore else 0), ctypes.byref(t)),
                 "autotune")
         return t.value
+
+    def _cbds(self, fn, what, core, out_core, out_set, want_set, want_core):
+        if want_set and out_set is None:
+            out_set = np.empty(max(self.n, 1), np.uint8)
+        if want_core and out_core is None and core is None:
+            out_core = np.empty(max(self.n, 1), np.uint32)
+        r = N.CbdsResult()
+        N.check(fn(self._h, N.ptr(_u32(core)), N.ptr(out_core), N.ptr(out_set) if want_set else None,
+                   ctypes.byref(r)), what)
+        if isinstance(out_set, np.ndarray):
+            out_set = out_set[:self.n]
+        if isinstance(out_core, np.ndarray):
+            out_core = out_core[:self.n]
+        return Cbds(r.k_star, r.E_core, r.V_core, r.E, r.V, r.n_legit, out_set if want_set else None,
+                    out_core if out_core is not None else core)
+
+    def densest_core(self, core=None, out_core=None, out_set=None, want_set: bool = True,
+                     want_core: bool = True) -> Cbds:
+        """Densest k-core (Sec. 3.2).  `core` (optional) replaces the core numbers."""
+        return self._cbds(lib().dsg_densest_core, "densest_core", core, out_core, out_set, want_set, want_core)
+
+    def cbds(self, core=None, out_core=None, out_set=None, want_set: bool = True, want_core: bool = True) -> Cbds:
+        """CBDS-P (Algorithm 2): densest core plus the second phase's legit vertices."""
+        return self._cbds(lib().dsg_cbds, "cbds", core, out_core, out_set, want_set, want_core)
 
     def tuning(self, kernel: str = "peel") -> dict:
         """Launch parameters a solve of `kernel` ("peel" or "kcore") on this graph uses now."""

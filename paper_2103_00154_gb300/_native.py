@@ -72,6 +72,11 @@ class ServeStats(c.Structure):
                 ("uptime_s", c.c_double)]
 
 
+class CbdsResult(c.Structure):
+    _fields_ = [("k_star", c.c_uint64), ("E_core", c.c_uint64), ("V_core", c.c_uint64), ("E", c.c_uint64),
+                ("V", c.c_uint64), ("n_legit", c.c_uint64)]
+
+
 _LIB = None
 
 # (name, restype, argtypes)
@@ -87,6 +92,8 @@ _SIGS = [
     ("dsg_round_bound", c.c_uint64, [c.c_uint32, c.c_uint32, c.c_uint32]),
     ("dsg_bahmani_noalloc", c.c_int, [c.c_uint32, _VP, _VP, c.c_uint32, c.c_uint32, _VP, _U64P, _U64P, _VP]),
     ("dsg_kcore", c.c_int, [_VP, _VP]),
+    ("dsg_densest_core", c.c_int, [_VP, _VP, _VP, _VP, c.POINTER(CbdsResult)]),
+    ("dsg_cbds", c.c_int, [_VP, _VP, _VP, _VP, c.POINTER(CbdsResult)]),
     ("dsg_batch_solve", c.c_int, [c.POINTER(Batch), c.POINTER(BatchResult), _VP]),
     ("dsg_serve_create", c.c_int, [c.POINTER(ServeConfig), c.POINTER(_VP)]),
     ("dsg_serve_submit", c.c_int, [_VP, c.POINTER(Request), _U64P]),
