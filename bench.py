@@ -83,6 +83,7 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cbds", action="store_true", help="skip the densest-core / CBDS-P timing")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-parameter autotuner before warm-up")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in the batch workload")
@@ -183,12 +184,61 @@ def peel_bytes(n: int, m: int, st: dict) -> int:
 
 def kcore_bytes(n: int, m: int, st: dict) -> int:
     """Algorithmic bytes of one core-number launch: adjacency 8m; offsets of
-    every frontier vertex 16n; degree init write 4n; per level the remaining
-    id + degree read 8|R_k| (level 0 reads no id); per adjacency entry one
-    degree read 4 B; each atomic (decrement or undo) 4 B write; remaining-list
-    writes 4 B each."""
-    return (8 * m + 16 * n + 4 * n + 8 * st["rem_scanned"] - 4 * n + 4 * 2 * m + 4 * st["atomics"]
-            + 4 * st["rem_written"])
+    every frontier vertex 16n; degree init write 4n and claim-bitmap clear
+    n/8; per level the remaining id, degree and claim word read 12|R_k|
+    (level 0 reads no id); one claim atomic per vertex 4n; per adjacency
+    entry one degree read 4 B; each degree atomic (decrement or undo) 4 B
+    write; remaining-list writes 4 B each."""
+    return (8 * m + 16 * n + 4 * n + n // 8 + 12 * st["rem_scanned"] - 4 * n + 4 * n + 4 * 2 * m
+            + 4 * st["atomics"] + 4 * st["rem_written"])
+
+
+def cbds_hist_bytes(n: int, m: int) -> int:
+    """Algorithmic bytes of the densest-core histogram pass: every vertex's
+    core number 4n and row start 8n, the adjacency 8m, and the neighbour's
+    core number of each edge taken once (u > v) 4m."""
+    return 12 * n + 12 * m
+
+
+def run_cbds_timing(args, g, core_d, set_d, flush, stream, n, m):
+    """Densest core + Algorithm 2's second phase on the step's graph, from
+    its core numbers (already on the device), timed like the step."""
+    import torch
+    import paper_2103_00154_gb300 as dsg
+    from paper_2103_00154_gb300 import _native as N
+    L = dsg.lib()
+    for _ in range(3):
+        r = g.cbds(core=core_d, out_set=set_d, want_core=False)
+    torch.cuda.synchronize()
+    L.dsg_profile_reset()
+    L.dsg_profile_enable(1)
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = g.cbds(core=core_d, out_set=set_d, want_core=False)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    L.dsg_profile_enable(0)
+    prof = N.profile_report()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if "cbds_core_hist" in prof:
+        cnt, tot = prof["cbds_core_hist"]
+        alg = cbds_hist_bytes(n, m)
+        achieved = alg / (tot / cnt * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "cbds_core_hist", "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "alg_bytes_per_launch": int(alg), "avg_launch_ms": round(tot / cnt, 4)}
+    return {"ms_per_call": round(sum(ms) / len(ms), 4), "kernel_ms": {k: round(v[1] / args.steps, 4)
+                                                                     for k, v in prof.items()},
+            "roofline": roof, "k_star": r.k_star, "E_core": r.E_core, "V_core": r.V_core, "E": r.E, "V": r.V,
+            "n_legit": r.n_legit,
+            "note": "dsg_cbds with the step's core numbers supplied on the device (densest core + second phase)"}
 
 
 # ----------------------------------------------------------------- our arm
@@ -308,6 +358,12 @@ def run_ours(args, wl, raw, rank, world):
         "tuning": tuning,
     }
 
+    if not args.no_cbds:
+        g = dsg.Graph.from_edges(n, src_d, dst_d, stream=stream)
+        g.kcore(out=core_d)
+        set_d = torch.empty(n, dtype=torch.uint8, device=dev)
+        out["cbds"] = run_cbds_timing(args, g, core_d, set_d, flush, stream, n, m)
+        g.close()
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, wl, raw, dev, edges_per_step, world)
     return out
@@ -704,6 +760,7 @@ def main():
             "peel_rounds": res["peel_rounds"],
             "kcore_counters": res["kcore"],
             "results": res["results"],
+            "cbds": res.get("cbds"),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

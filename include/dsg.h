@@ -309,6 +309,11 @@ dsg_status dsg_set_hot_degree(uint32_t hot_deg);
  * to the grid-wide frontier of the next sub-round.  Defaults 1024 / 16384;
  * DSG_LOCAL_MAX, DSG_LOCAL_WORK.  Results never depend on them. */
 dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work);
+/* Core numbers: a vertex whose row has at most inline_max entries and that a
+ * block's level scan finds at the level is drained by that block in the same
+ * sub-round; longer rows are spread over every warp in the next sub-round.
+ * Default 4096; DSG_INLINE_MAX.  Results never depend on it. */
+dsg_status dsg_set_inline_max(uint32_t inline_max);
 
 /*
  * Densest k-core and CBDS-P (Algorithm 2).
@@ -354,8 +359,9 @@ dsg_status dsg_cbds(const dsg_graph* g, const uint32_t* core, uint32_t* out_core
  * Autotuner.  dsg_autotune times candidate launch parameters for the peel
  * (what bit 0, at eps_num/eps_den) and/or the core numbers (bit 1) on graph g
  * by coordinate descent over block size, hub threshold, chunk length and
- * short-row limit (peel) or block size, hub threshold and the local-drain
- * limits (core numbers), keeping a change only when it is at least 2%
+ * short-row limit (peel) or block size, hub threshold, the local-drain
+ * limits and the inline-drain limit (core numbers), keeping a change only
+ * when it is at least 2%
  * faster.  The winner is recorded for g's size class (floor log2 n,
  * floor log2 2m) on this device and used by every later solve of a graph of
  * that class; *trials gets the number of timed solves.  The table is saved
@@ -369,8 +375,23 @@ void dsg_tune_clear(void);
 uint32_t dsg_tune_entries(void);
 /* The launch parameters a solve of kernel 0 (peel) or 1 (core numbers) on g
  * would use now: out = {block, blocks_per_sm, short_max, chunk_len, hot_deg,
- * local_max, local_work}. */
-dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[7]);
+ * local_max, local_work, inline_max}. */
+dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[8]);
+
+/*
+ * Device-memory allocator hook (no counterpart in the paper; lets a host
+ * framework's caching allocator own every device buffer the library makes:
+ * graph CSR arrays and per-call scratch).  alloc(bytes, ctx, stream) returns
+ * device memory of the current device usable in stream order on `stream`
+ * (NULL = out of memory, reported as DSG_ENOMEM); free(ptr, ctx, stream)
+ * takes it back in stream order.  Each pointer returns to the allocator that
+ * made it, so the hook may be changed between calls; passing NULL for either
+ * function restores the built-in stream-ordered pool.  Process-wide; do not
+ * change it while a call is running on another thread.
+ */
+typedef void* (*dsg_alloc_fn)(size_t bytes, void* ctx, void* stream);
+typedef void (*dsg_free_fn)(void* ptr, void* ctx, void* stream);
+void dsg_set_allocator(dsg_alloc_fn alloc, dsg_free_fn free_fn, void* ctx);
 
 /* Upper bound (ns) on every device-side wait (grid barriers, queue polls).
  * A wait that runs out makes its kernel return and the call report

@@ -32,10 +32,11 @@ def round_bound(n: int, p: int, q: int) -> int:
 
 
 def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, chunk_len: int = 256,
-               hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384):
+               hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384, inline_max: int = 4096):
     N.check(lib().dsg_set_tuning(block, blocks_per_sm, short_max, chunk_len), "set_tuning")
     N.check(lib().dsg_set_hot_degree(hot_deg), "set_hot_degree")
     N.check(lib().dsg_set_local_max(local_max, local_work), "set_local_max")
+    N.check(lib().dsg_set_inline_max(inline_max), "set_inline_max")
 
 
 def get_tuning():
@@ -60,6 +61,34 @@ def tune_clear():
 
 def tune_entries() -> int:
     return int(lib().dsg_tune_entries())
+
+
+_alloc_hooks = None
+
+
+def use_torch_allocator(on: bool = True):
+    """Route every device buffer the library makes through PyTorch's caching
+    allocator (dsg_set_allocator), or back to the library's own pool."""
+    global _alloc_hooks
+    if not on:
+        lib().dsg_set_allocator(N.ALLOC_FN(), N.FREE_FN(), None)
+        _alloc_hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, ctx, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(max(int(nbytes), 1), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:  # out of memory -> NULL -> DSG_ENOMEM
+            return None
+
+    def _free(ptr, ctx, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    hooks = (N.ALLOC_FN(_alloc), N.FREE_FN(_free))
+    lib().dsg_set_allocator(hooks[0], hooks[1], None)
+    _alloc_hooks = hooks  # keep the callbacks alive
 
 
 def set_wait_limit_ns(ns: int):
@@ -237,10 +266,10 @@ class Graph:
 
     def tuning(self, kernel: str = "peel") -> dict:
         """Launch parameters a solve of `kernel` ("peel" or "kcore") on this graph uses now."""
-        v = (ctypes.c_uint32 * 7)()
+        v = (ctypes.c_uint32 * 8)()
         N.check(lib().dsg_tune_lookup(self._h, 0 if kernel == "peel" else 1, v), "tune_lookup")
-        return dict(zip(("block", "blocks_per_sm", "short_max", "chunk_len", "hot_deg", "local_max", "local_work"),
-                        list(v)))
+        return dict(zip(("block", "blocks_per_sm", "short_max", "chunk_len", "hot_deg", "local_max", "local_work",
+                         "inline_max"), list(v)))
 
     def kcore(self, out=None):
         """Core numbers (Algorithm 2, first phase)."""

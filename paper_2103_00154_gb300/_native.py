@@ -77,6 +77,9 @@ class CbdsResult(c.Structure):
                 ("V", c.c_uint64), ("n_legit", c.c_uint64)]
 
 
+ALLOC_FN = c.CFUNCTYPE(c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p)
+FREE_FN = c.CFUNCTYPE(None, c.c_void_p, c.c_void_p, c.c_void_p)
+
 _LIB = None
 
 # (name, restype, argtypes)
@@ -112,6 +115,8 @@ _SIGS = [
     ("dsg_tune_clear", None, []),
     ("dsg_tune_entries", c.c_uint32, []),
     ("dsg_tune_lookup", c.c_int, [_VP, c.c_uint32, _U32P]),
+    ("dsg_set_inline_max", c.c_int, [c.c_uint32]),
+    ("dsg_set_allocator", None, [ALLOC_FN, FREE_FN, _VP]),
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),
     ("dsg_debug_peel_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, _U64P, c.c_uint64, _U64P]),
     ("dsg_debug_kcore_trace", c.c_int, [_VP, _U64P, c.c_uint64, _U64P]),

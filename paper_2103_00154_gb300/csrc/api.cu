@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <unordered_map>
 
 #include "dsg_common.cuh"
 #include "dsg_kernels.cuh"
@@ -49,7 +50,32 @@ static cudaError_t pool_for(int dev, cudaMemPool_t* out) {
     return cudaSuccess;
 }
 
+// Caller-installed allocator (dsg_set_allocator); pointers it handed out are
+// remembered so each goes back to the allocator that made it.
+struct HookAlloc {
+    dsg_alloc_fn alloc = nullptr;
+    dsg_free_fn free = nullptr;
+    void* ctx = nullptr;
+};
+static std::mutex g_hook_mu;
+static HookAlloc g_hook;
+static std::unordered_map<void*, HookAlloc>* g_hook_ptrs = nullptr;
+
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    HookAlloc h;
+    {
+        std::lock_guard<std::mutex> lk(g_hook_mu);
+        h = g_hook;
+    }
+    if (h.alloc) {
+        void* q = h.alloc(bytes, h.ctx, (void*)s);
+        if (!q) return cudaErrorMemoryAllocation;
+        std::lock_guard<std::mutex> lk(g_hook_mu);
+        if (!g_hook_ptrs) g_hook_ptrs = new std::unordered_map<void*, HookAlloc>();
+        (*g_hook_ptrs)[q] = h;
+        *p = q;
+        return cudaSuccess;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -61,6 +87,21 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
 
 cudaError_t dev_free(void* p, cudaStream_t s) {
     if (!p) return cudaSuccess;
+    HookAlloc h;
+    {
+        std::lock_guard<std::mutex> lk(g_hook_mu);
+        if (g_hook_ptrs) {
+            auto it = g_hook_ptrs->find(p);
+            if (it != g_hook_ptrs->end()) {
+                h = it->second;
+                g_hook_ptrs->erase(it);
+            }
+        }
+    }
+    if (h.free) {
+        h.free(p, h.ctx, (void*)s);
+        return cudaSuccess;
+    }
     return cudaFreeAsync(p, s);
 }
 
@@ -257,3 +298,14 @@ dsg_status dsg_graph_from_csr(uint32_t n, const uint64_t* off, const uint32_t* a
 }
 
 }  // extern "C"
+
+extern "C" void dsg_set_allocator(dsg_alloc_fn alloc, dsg_free_fn free_fn, void* ctx) {
+    std::lock_guard<std::mutex> lk(g_hook_mu);
+    if (alloc && free_fn) {
+        g_hook.alloc = alloc;
+        g_hook.free = free_fn;
+        g_hook.ctx = ctx;
+    } else {
+        g_hook = HookAlloc();
+    }
+}

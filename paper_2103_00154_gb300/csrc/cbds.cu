@@ -55,11 +55,15 @@ struct __align__(128) CbdsCtl {
 // ------------------------------------------------------------- edge walker
 // Visit every adjacency entry j in [0, off[n]) as (v = row owner, u = adj[j]).
 // Each warp takes one contiguous span of entries, finds the row of its first
-// entry by binary search over off, and then moves through the span 32
-// consecutive entries at a time; a lane finds its entry's row among the next
-// 32 row starts (loaded by the warp in one coalesced read) with a 5-step
-// shuffle search, taking further windows only past runs of empty rows.
-// fn(v, u, active) is called by all lanes together.
+// entry by binary search over off, and then moves through the span kWalkU * 32
+// consecutive entries at a time (lane l takes entries l, l + 32, ...): the
+// adjacency loads of a step are issued together, and a lane finds each
+// entry's row among the next 32 row starts (one coalesced read by the warp)
+// with a 5-step shuffle search, taking further windows only past runs of
+// empty rows.  fn(v[], u[], valid) is called by all lanes together, bit t of
+// valid set when slot t holds an entry.
+constexpr uint32_t kWalkU = 4;
+
 template <class Fn>
 __device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
                                                  uint32_t n, Fn& fn) {
@@ -67,8 +71,9 @@ __device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ of
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr uint32_t kStep = 32 * kWalkU;
     uint64_t span = (total + nw - 1) / nw;
-    span = span < 256 ? 256 : ((span + 31) & ~31ull);
+    span = span < 2 * kStep ? 2 * kStep : ((span + kStep - 1) / kStep * kStep);
     const uint64_t j0 = gw * span;
     if (j0 >= total) return;
     const uint64_t j1 = min(total, j0 + span);
@@ -79,37 +84,47 @@ __device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ of
         if (off[mid] <= j0) lo = mid; else hi = mid;
     }
     uint32_t r = lo;
-    for (uint64_t jb = j0; jb < j1; jb += 32) {
-        const uint64_t j = jb + lane;
-        const bool act = j < j1;
-        uint32_t owner = r;
-        bool done = !act;
+    for (uint64_t jb = j0; jb < j1; jb += kStep) {
+        uint64_t j[kWalkU];
+        uint32_t u[kWalkU], owner[kWalkU], valid = 0, done = 0;
+#pragma unroll
+        for (uint32_t t = 0; t < kWalkU; ++t) {
+            j[t] = jb + lane + 32 * t;
+            owner[t] = r;
+            u[t] = 0;
+            if (j[t] < j1) {
+                valid |= 1u << t;
+                u[t] = adj[j[t]];
+            }
+        }
+        done = ~valid & ((1u << kWalkU) - 1);
         uint32_t base = r;
         while (true) {
             const uint32_t idx = base + 1 + lane;
             const uint64_t w = off[idx < n ? idx : n];
             const uint64_t w31 = __shfl_sync(kFullMask, w, 31);
-            uint32_t c = 0;
 #pragma unroll
-            for (uint32_t step = 16; step > 0; step >>= 1) {
-                const uint64_t wv = __shfl_sync(kFullMask, w, c + step - 1);
-                if (wv <= j) c += step;
+            for (uint32_t t = 0; t < kWalkU; ++t) {
+                uint32_t c = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1) {
+                    const uint64_t wv = __shfl_sync(kFullMask, w, c + step - 1);
+                    if (wv <= j[t]) c += step;
+                }
+                if (c == 31 && w31 <= j[t]) c = 32;
+                if (!(done >> t & 1u) && c < 32) {
+                    owner[t] = base + c;
+                    done |= 1u << t;
+                }
             }
-            if (c == 31 && w31 <= j) c = 32;
-            if (!done && c < 32) {
-                owner = base + c;
-                done = true;
-            }
-            if (__all_sync(kFullMask, done)) break;
+            if (__all_sync(kFullMask, done == (1u << kWalkU) - 1)) break;
             base += 32;
         }
-        const uint32_t u = act ? adj[j] : 0u;
-        fn(owner, u, act);
-        r = __shfl_sync(kFullMask, owner, 31);
-        if (!__shfl_sync(kFullMask, (uint32_t)act, 31)) {
-            // last lane inactive only on the span's final step
-            break;
-        }
+        fn(owner, u, valid);
+        // next step starts at or after the row of this step's last entry
+        const uint32_t last = valid >> (kWalkU - 1) & 1u ? owner[kWalkU - 1] : r;
+        r = __shfl_sync(kFullMask, last, 31);
+        if (!__shfl_sync(kFullMask, valid >> (kWalkU - 1) & 1u, 31)) break;  // span's final step
     }
 }
 
@@ -162,10 +177,19 @@ __global__ void __launch_bounds__(kHistTB) core_hist_kernel(const uint64_t* __re
         if (use_sh) hist_add_shared(sh.hv, key); else hist_add_global(hV, key);
     }
     // edges, each once (entry (v, u) with u > v): hE[min(core(v), core(u))]
-    auto visit = [&](uint32_t v, uint32_t u, bool act) {
-        uint32_t key = ~0u;
-        if (act && u > v) key = min(core[v], core[u]);
-        if (use_sh) hist_add_shared(sh.he, key); else hist_add_global(hE, key);
+    auto visit = [&](const uint32_t* v, const uint32_t* u, uint32_t valid) {
+        uint32_t cv[kWalkU], cu[kWalkU];
+#pragma unroll
+        for (uint32_t t = 0; t < kWalkU; ++t) {
+            const bool take = (valid >> t & 1u) && u[t] > v[t];
+            cv[t] = take ? core[v[t]] : ~0u;
+            cu[t] = take ? core[u[t]] : ~0u;
+        }
+#pragma unroll
+        for (uint32_t t = 0; t < kWalkU; ++t) {
+            const uint32_t key = min(cv[t], cu[t]);
+            if (use_sh) hist_add_shared(sh.he, key); else hist_add_global(hE, key);
+        }
     };
     walk_all_entries(off, adj, n, visit);
     if (use_sh) {
@@ -341,6 +365,15 @@ __global__ void legit_mark_kernel(const uint64_t* __restrict__ off, const uint32
 
 uint32_t grid_for(uint32_t per_sm) { return (uint32_t)dev_info().sms * per_sm; }
 
+// Full-occupancy grid for a kernel of kHistTB threads (at least one block per SM).
+template <class K>
+uint32_t occ_grid(K kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kHistTB, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return grid_for((uint32_t)per_sm);
+}
+
 }  // namespace
 
 // Densest core (and, with phase2, the augmentation) of g for the core
@@ -376,7 +409,7 @@ static dsg_status run_cbds(const dsg_graph* g, const uint32_t* core_dev, bool ph
     DSG_TRY_CUDA(cudaMemsetAsync(hE, 0, K * 8, s));
     {
         LaunchScope ls("cbds_core_hist", s);
-        core_hist_kernel<<<grid, kHistTB, 0, s>>>(g->off, g->adj, core_dev, n, ctl, hV, hE);
+        core_hist_kernel<<<occ_grid(core_hist_kernel), kHistTB, 0, s>>>(g->off, g->adj, core_dev, n, ctl, hV, hE);
     }
     {
         LaunchScope ls("cbds_densest_pick", s);

@@ -20,6 +20,8 @@ struct Tuning {
                                 // several times by every block)
     uint32_t local_max = 1024;  // k-core: rows up to this length reached while draining stay in the block
     uint32_t local_work = 16384; // k-core: ... while that block's local share of the sub-round stays within this
+    uint32_t inline_max = 4096;  // k-core: rows up to this length claimed by a block's level scan are drained by
+                                 // that block; longer ones by every warp in the next sub-round
 };
 
 Tuning current_tuning();
@@ -198,6 +200,52 @@ __device__ __forceinline__ void scan_block_list(const uint64_t* __restrict__ off
     }
 }
 
+// scan_block_list over rows whose starts and lengths are already known:
+// rows F[0, cnt) with row starts B[] and lengths L[].
+template <int TB, class Fn>
+__device__ __forceinline__ void scan_block_rows(const uint32_t* __restrict__ adj, const uint32_t* F,
+                                                const uint64_t* B, const uint32_t* L, uint32_t cnt_all,
+                                                BlockTile<TB>& sm, Fn& fn) {
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t t = 0; t < cnt_all; t += TB) {
+        const uint32_t cnt = min((uint32_t)TB, cnt_all - t);
+        uint32_t v = 0, len = 0;
+        uint64_t b = 0;
+        if (tid < cnt) {
+            v = F[t + tid];
+            b = B[t + tid];
+            len = L[t + tid];
+        }
+        uint32_t total;
+        const uint32_t st = block_excl_scan<uint32_t>(len, sm.scan_tmp, &total);
+        sm.start[tid] = st;
+        sm.beg[tid] = b;
+        sm.v[tid] = v;
+        __syncthreads();
+        for (uint32_t e0 = tid; e0 < total; e0 += kBatch * TB) {
+            uint32_t bu[kBatch], bv[kBatch], valid = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < kBatch; ++j) {
+                const uint32_t e = e0 + j * TB;
+                bu[j] = 0;
+                bv[j] = 0;
+                if (e < total) {
+                    uint32_t a = 0, z = cnt;  // owner = last row whose start is <= e
+                    while (z - a > 1) {
+                        const uint32_t mid = (a + z) >> 1;
+                        if (sm.start[mid] <= e) a = mid; else z = mid;
+                    }
+                    bu[j] = adj[sm.beg[a] + (e - sm.start[a])];
+                    bv[j] = sm.v[a];
+                    valid |= 1u << j;
+                }
+            }
+            fn(bu, bv, valid);
+        }
+        __syncthreads();
+    }
+}
+
 // Walk every adjacency entry of a frontier, handing entries to the visitor
 // four at a time per thread so the visitor can issue four independent loads
 // (then four independent atomics) before it waits on any of them.  No block
@@ -214,11 +262,14 @@ __device__ __forceinline__ void scan_block_list(const uint64_t* __restrict__ off
 // together (valid may be 0).
 // LOCAL = true: F is this block's own list (e.g. in shared memory) and only
 // this block's warps walk it; C is ignored.
+// FB / FL (nullable): row starts and lengths stored beside F, saving the
+// offset loads of the short rows.
 template <int TB, bool LOCAL = false, class Fn>
 __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
                                               const uint32_t* F, uint64_t lo, uint64_t hi,
                                               const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
-                                              uint32_t chunk_len, Fn& fn, uint32_t dbg_n = 0) {
+                                              uint32_t chunk_len, Fn& fn, uint32_t dbg_n = 0,
+                                              const uint64_t* FB = nullptr, const uint32_t* FL = nullptr) {
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31u;
     const uint64_t gw = LOCAL ? (uint64_t)(tid >> 5) : ((uint64_t)blockIdx.x * TB + tid) >> 5;
@@ -237,8 +288,13 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
                 v = 0;
             }
 #endif
-            b = off[v];
-            len = (uint32_t)(off[v + 1] - b);
+            if (FB) {
+                b = FB[i];
+                len = FL[i];
+            } else {
+                b = off[v];
+                len = (uint32_t)(off[v + 1] - b);
+            }
         }
         const uint32_t inc = warp_incl_scan(len);
         const uint32_t total = __shfl_sync(kFullMask, inc, 31);

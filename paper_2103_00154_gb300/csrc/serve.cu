@@ -5,12 +5,12 @@
 //           it (DSG_EBUSY when the queue is full: back-pressure);
 //   worker  (one host thread per server) admits queued requests while their
 //           device-memory charge fits the budget, ingests each on the ingest
-//           stream into a resident graph, and whenever no batch is running
-//           launches one block-per-graph launch over everything ingested so
-//           far on the solve stream; while that batch runs it keeps
-//           admitting and ingesting new arrivals, which form the next batch;
-//           a finished batch's results are copied out, its graphs freed and
-//           their charge returned to the budget;
+//           stream into a resident graph, and whenever one of its
+//           max_inflight solve streams is free launches one block-per-graph
+//           launch over everything ingested so far on that stream; while
+//           batches run it keeps admitting and ingesting new arrivals, which
+//           form the next batch; a finished batch's results are copied out,
+//           its graphs freed and their charge returned to the budget;
 //   poll    waits (bounded) for one ticket's completion.
 // A request's results do not depend on what it is batched with: each graph is
 // solved by its own block with its own state.

@@ -32,6 +32,7 @@ Tuning current_tuning() {
         t.hot_deg = env_u32("DSG_HOT_DEG", t.hot_deg);
         t.local_max = env_u32("DSG_LOCAL_MAX", t.local_max);
         t.local_work = env_u32("DSG_LOCAL_WORK", t.local_work);
+        t.inline_max = env_u32("DSG_INLINE_MAX", t.inline_max);
         if (t.block != 256 && t.block != 512 && t.block != 1024) t.block = 512;
         if (t.chunk_len < 32) t.chunk_len = 32;
         if (t.short_max < 1) t.short_max = 1;
@@ -73,6 +74,14 @@ extern "C" dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.local_max = local_max;
     g_tune.local_work = local_work;
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_set_inline_max(uint32_t inline_max) {
+    clear_error();
+    current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.inline_max = inline_max;
     return DSG_OK;
 }
 
@@ -164,6 +173,7 @@ static int load_table_locked(const char* path) {
         parse_u32(obj.c_str(), "hot_deg", &t.hot_deg);
         parse_u32(obj.c_str(), "local_max", &t.local_max);
         parse_u32(obj.c_str(), "local_work", &t.local_work);
+        parse_u32(obj.c_str(), "inline_max", &t.inline_max);
         if ((t.block == 256 || t.block == 512 || t.block == 1024) && t.chunk_len >= 32 && t.short_max >= 1) {
             g_table[key] = t;
             ++loaded;
@@ -260,9 +270,11 @@ extern "C" dsg_status dsg_autotune(const dsg_graph* g, uint32_t eps_num, uint32_
         const Knob core_knobs[] = {{&Tuning::block, {256, 512, 1024}, 3},
                                    {&Tuning::hot_deg, {0, 1024, 4096, 16384}, 4},
                                    {&Tuning::local_max, {256, 1024, 4096}, 3},
-                                   {&Tuning::local_work, {4096, 16384, 65536}, 3}};
+                                   {&Tuning::local_work, {4096, 16384, 65536}, 3},
+                                   {&Tuning::inline_max, {256, 1024, 4096, 16384}, 4}};
         const Knob* knobs = kernel == 0 ? peel_knobs : core_knobs;
-        for (int kk = 0; kk < 4; ++kk) {
+        const int nknobs = kernel == 0 ? 4 : 5;
+        for (int kk = 0; kk < nknobs; ++kk) {
             for (int vi = 0; vi < knobs[kk].count; ++vi) {
                 Tuning cand = best;
                 cand.*(knobs[kk].field) = knobs[kk].values[vi];
@@ -307,9 +319,10 @@ extern "C" dsg_status dsg_tune_save(const char* path) {
         auto ms = g_table_ms.find(kv.first);
         fprintf(f,
                 "  {\"key\": \"%s\", \"block\": %u, \"blocks_per_sm\": %u, \"short_max\": %u, \"chunk_len\": %u, "
-                "\"hot_deg\": %u, \"local_max\": %u, \"local_work\": %u, \"ms\": %.4f}%s\n",
+                "\"hot_deg\": %u, \"local_max\": %u, \"local_work\": %u, \"inline_max\": %u, \"ms\": %.4f}%s\n",
                 kv.first.c_str(), t.block, t.blocks_per_sm, t.short_max, t.chunk_len, t.hot_deg, t.local_max,
-                t.local_work, ms == g_table_ms.end() ? -1.0 : ms->second, ++i < g_table.size() ? "," : "");
+                t.local_work, t.inline_max, ms == g_table_ms.end() ? -1.0 : ms->second,
+                ++i < g_table.size() ? "," : "");
     }
     fprintf(f, "]}\n");
     fclose(f);
@@ -346,12 +359,13 @@ extern "C" uint32_t dsg_tune_entries(void) {
     return (uint32_t)g_table.size();
 }
 
-extern "C" dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[7]) {
+extern "C" dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[8]) {
     clear_error();
     DSG_CHECK_ARG(g && out, "graph or out is NULL");
     DSG_CHECK_ARG(kernel <= 1, "kernel must be 0 (peel) or 1 (core numbers)");
     const Tuning t = tuning_for(g, (int)kernel);
-    const uint32_t v[7] = {t.block, t.blocks_per_sm, t.short_max, t.chunk_len, t.hot_deg, t.local_max, t.local_work};
+    const uint32_t v[8] = {t.block,     t.blocks_per_sm, t.short_max,  t.chunk_len,
+                           t.hot_deg,   t.local_max,     t.local_work, t.inline_max};
     memcpy(out, v, sizeof(v));
     return DSG_OK;
 }

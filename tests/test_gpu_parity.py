@@ -247,6 +247,17 @@ def test_long_chains_overflow_the_block_queue():
         check_core(gpu_graph(r2), c2, f"rmat chain {block}/{local_max}")
 
 
+@pytest.mark.parametrize("inline_max,local_work", [(0, 16384), (256, 0), (16384, 1 << 30), (1 << 30, 4096)])
+def test_core_numbers_do_not_depend_on_where_rows_are_drained(inline_max, local_work):
+    # scan-found rows drained by the finding block or by every warp, cascades
+    # in the block or grid-wide: the same core numbers
+    for raw in (inputs.chung_lu(n=1 << 14, m_draws=1 << 18, gamma=2.1, mean=32.0, wmax=6000.0, seed=12),
+                inputs.union(inputs.rmat(scale=13, m=1 << 17, seed=13), inputs.block(1 << 13, 120, 0.5, 13))):
+        c = oracle.from_raw(raw)
+        dsg.set_tuning(inline_max=inline_max, local_work=local_work)
+        check_core(gpu_graph(raw), c, f"inline {inline_max}/{local_work}")
+
+
 def test_from_csr_paths():
     raw = inputs.er_block(n=2000, m=9000, k=40, p=0.5, seed=9)
     c = oracle.from_raw(raw)
