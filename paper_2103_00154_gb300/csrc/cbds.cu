@@ -52,82 +52,6 @@ struct __align__(128) CbdsCtl {
     uint64_t n_elig_items, n_legit_items;
 };
 
-// ------------------------------------------------------------- edge walker
-// Visit every adjacency entry j in [0, off[n]) as (v = row owner, u = adj[j]).
-// Each warp takes one contiguous span of entries, finds the row of its first
-// entry by binary search over off, and then moves through the span kWalkU * 32
-// consecutive entries at a time (lane l takes entries l, l + 32, ...): the
-// adjacency loads of a step are issued together, and a lane finds each
-// entry's row among the next 32 row starts (one coalesced read by the warp)
-// with a 5-step shuffle search, taking further windows only past runs of
-// empty rows.  fn(v[], u[], valid) is called by all lanes together, bit t of
-// valid set when slot t holds an entry.
-constexpr uint32_t kWalkU = 4;
-
-template <class Fn>
-__device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
-                                                 uint32_t n, Fn& fn) {
-    const uint64_t total = off[n];
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    constexpr uint32_t kStep = 32 * kWalkU;
-    uint64_t span = (total + nw - 1) / nw;
-    span = span < 2 * kStep ? 2 * kStep : ((span + kStep - 1) / kStep * kStep);
-    const uint64_t j0 = gw * span;
-    if (j0 >= total) return;
-    const uint64_t j1 = min(total, j0 + span);
-    // row r with off[r] <= j0 < off[r + 1]
-    uint32_t lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (off[mid] <= j0) lo = mid; else hi = mid;
-    }
-    uint32_t r = lo;
-    for (uint64_t jb = j0; jb < j1; jb += kStep) {
-        uint64_t j[kWalkU];
-        uint32_t u[kWalkU], owner[kWalkU], valid = 0, done = 0;
-#pragma unroll
-        for (uint32_t t = 0; t < kWalkU; ++t) {
-            j[t] = jb + lane + 32 * t;
-            owner[t] = r;
-            u[t] = 0;
-            if (j[t] < j1) {
-                valid |= 1u << t;
-                u[t] = adj[j[t]];
-            }
-        }
-        done = ~valid & ((1u << kWalkU) - 1);
-        uint32_t base = r;
-        while (true) {
-            const uint32_t idx = base + 1 + lane;
-            const uint64_t w = off[idx < n ? idx : n];
-            const uint64_t w31 = __shfl_sync(kFullMask, w, 31);
-#pragma unroll
-            for (uint32_t t = 0; t < kWalkU; ++t) {
-                uint32_t c = 0;
-#pragma unroll
-                for (uint32_t step = 16; step > 0; step >>= 1) {
-                    const uint64_t wv = __shfl_sync(kFullMask, w, c + step - 1);
-                    if (wv <= j[t]) c += step;
-                }
-                if (c == 31 && w31 <= j[t]) c = 32;
-                if (!(done >> t & 1u) && c < 32) {
-                    owner[t] = base + c;
-                    done |= 1u << t;
-                }
-            }
-            if (__all_sync(kFullMask, done == (1u << kWalkU) - 1)) break;
-            base += 32;
-        }
-        fn(owner, u, valid);
-        // next step starts at or after the row of this step's last entry
-        const uint32_t last = valid >> (kWalkU - 1) & 1u ? owner[kWalkU - 1] : r;
-        r = __shfl_sync(kFullMask, last, 31);
-        if (!__shfl_sync(kFullMask, valid >> (kWalkU - 1) & 1u, 31)) break;  // span's final step
-    }
-}
-
 // Warp-aggregated histogram increment: lanes holding the same key combine
 // their counts before one atomic.  key == ~0u means "no increment".
 __device__ __forceinline__ void hist_add_shared(uint32_t* h, uint32_t key) {
@@ -177,7 +101,8 @@ __global__ void __launch_bounds__(kHistTB) core_hist_kernel(const uint64_t* __re
         if (use_sh) hist_add_shared(sh.hv, key); else hist_add_global(hV, key);
     }
     // edges, each once (entry (v, u) with u > v): hE[min(core(v), core(u))]
-    auto visit = [&](const uint32_t* v, const uint32_t* u, uint32_t valid) {
+    auto pre = [&](uint64_t j) { return adj[j]; };
+    auto visit = [&](const uint32_t* v, const uint64_t*, const uint32_t* u, uint32_t valid) {
         uint32_t cv[kWalkU], cu[kWalkU];
 #pragma unroll
         for (uint32_t t = 0; t < kWalkU; ++t) {
@@ -191,7 +116,7 @@ __global__ void __launch_bounds__(kHistTB) core_hist_kernel(const uint64_t* __re
             if (use_sh) hist_add_shared(sh.he, key); else hist_add_global(hE, key);
         }
     };
-    walk_all_entries(off, adj, n, visit);
+    walk_all_entries(off, n, pre, visit);
     if (use_sh) {
         __syncthreads();
         const uint32_t kmax = ctl->kmax;

@@ -246,6 +246,93 @@ __device__ __forceinline__ void scan_block_rows(const uint32_t* __restrict__ adj
     }
 }
 
+// ------------------------------------------------------------- edge walker
+// Visit every adjacency position j in [0, off[n]) with its row owner.
+// Each warp takes one contiguous span of positions, finds the row of its first
+// position by binary search over off, and then moves through the span
+// kWalkU * 32 consecutive positions at a time (lane l takes l, l + 32, ...):
+// pre(j) is issued for every position of a step before the owners are
+// searched (so its loads overlap the search), and a lane finds each
+// position's row among the next 32 row starts (one coalesced read by the
+// warp) with a 5-step shuffle search, or -- past a run of empty rows -- by a
+// binary search over the row starts above them.
+// fn(owner[], j[], pre[], valid) is called by all lanes together, bit t of
+// valid set when slot t holds a position.
+constexpr uint32_t kWalkU = 4;
+
+template <class Pre, class Fn>
+__device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ off, uint32_t n, Pre& pre, Fn& fn) {
+    const uint64_t total = off[n];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr uint32_t kStep = 32 * kWalkU;
+    uint64_t span = (total + nw - 1) / nw;
+    span = span < 2 * kStep ? 2 * kStep : ((span + kStep - 1) / kStep * kStep);
+    const uint64_t j0 = gw * span;
+    if (j0 >= total) return;
+    const uint64_t j1 = min(total, j0 + span);
+    // row r with off[r] <= j0 < off[r + 1]
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (off[mid] <= j0) lo = mid; else hi = mid;
+    }
+    uint32_t r = lo;
+    for (uint64_t jb = j0; jb < j1; jb += kStep) {
+        uint64_t j[kWalkU];
+        uint32_t pv[kWalkU], owner[kWalkU], valid = 0, done = 0;
+#pragma unroll
+        for (uint32_t t = 0; t < kWalkU; ++t) {
+            j[t] = jb + lane + 32 * t;
+            owner[t] = r;
+            pv[t] = 0;
+            if (j[t] < j1) {
+                valid |= 1u << t;
+                pv[t] = pre(j[t]);
+            }
+        }
+        done = ~valid & ((1u << kWalkU) - 1);
+        {
+            const uint32_t base = r;
+            const uint32_t idx = base + 1 + lane;
+            const uint64_t w = off[idx < n ? idx : n];
+            const uint64_t w31 = __shfl_sync(kFullMask, w, 31);
+#pragma unroll
+            for (uint32_t t = 0; t < kWalkU; ++t) {
+                uint32_t c = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1) {
+                    const uint64_t wv = __shfl_sync(kFullMask, w, c + step - 1);
+                    if (wv <= j[t]) c += step;
+                }
+                if (c == 31 && w31 <= j[t]) c = 32;
+                if (!(done >> t & 1u) && c < 32) {
+                    owner[t] = base + c;
+                    done |= 1u << t;
+                }
+            }
+            // past a run of empty rows: binary search above the window
+            // (off[base + 32] <= j < off[n])
+#pragma unroll
+            for (uint32_t t = 0; t < kWalkU; ++t) {
+                if (done >> t & 1u) continue;
+                uint32_t a = base + 32, z = n;
+                while (z - a > 1) {
+                    const uint32_t mid = a + ((z - a) >> 1);
+                    if (off[mid] <= j[t]) a = mid; else z = mid;
+                }
+                owner[t] = a;
+            }
+        }
+        fn(owner, j, pv, valid);
+        // next step starts at or after the row of this step's last position
+        const uint32_t last = valid >> (kWalkU - 1) & 1u ? owner[kWalkU - 1] : r;
+        r = __shfl_sync(kFullMask, last, 31);
+        if (!__shfl_sync(kFullMask, valid >> (kWalkU - 1) & 1u, 31)) break;  // span's final step
+    }
+}
+
 // Walk every adjacency entry of a frontier, handing entries to the visitor
 // four at a time per thread so the visitor can issue four independent loads
 // (then four independent atomics) before it waits on any of them.  No block

@@ -2,8 +2,11 @@
 // E a set of edges between distinct vertices).
 //
 //   1. count   every non-loop pair adds one to the row of each endpoint
+//              (frequent endpoints, found from a sample of the pairs, are
+//              counted per block in shared memory)
 //   2. scan    row starts of the (still repeated) entries
-//   3. scatter each pair is written into both rows
+//   3. scatter each pair is written into both rows (a frequent endpoint's
+//              entries from one block go to a range reserved for that block)
 //   4. sort    each row sorted and de-duplicated in place; rows are binned by
 //              length: <= 32 entries one warp, one value per lane; <= 1024
 //              one warp holding up to 32 values per lane (register bitonic
@@ -29,12 +32,12 @@ namespace dsg {
 
 constexpr uint32_t kPad = 0xffffffffu;
 constexpr uint32_t kScanTile = 2048;
-constexpr uint32_t kBlockRowMax = 8192;  // longest row sorted by one block
-constexpr uint32_t kBlockWarps = kBlockRowMax / 1024;
+constexpr uint32_t kBlockRowMax = 8192;  // longest row sorted by one block (8 warps x 1024)
 constexpr uint32_t kWinBits = 13;        // giant rows: value windows of 8192 ids
 constexpr uint32_t kWin = 1u << kWinBits;
 constexpr uint32_t kWinWords = kWin / 32;
-constexpr int kClasses = 7;              // 0..4: warp rows E = 2..32, 5: block rows, 6: giant rows
+constexpr int kClasses = 9;              // 0..4: warp rows E = 2..32, 5..7: block rows of 2/4/8 warps, 8: giant
+constexpr int kGiant = 8;
 
 __global__ void validate_off_kernel(uint32_t n, const uint64_t* __restrict__ off, uint32_t* bad);
 
@@ -54,8 +57,10 @@ __device__ __forceinline__ int row_class(uint32_t len) {
     if (len <= 256) return 2;
     if (len <= 512) return 3;
     if (len <= 1024) return 4;
-    if (len <= kBlockRowMax) return 5;
-    return 6;
+    if (len <= 2048) return 5;
+    if (len <= 4096) return 6;
+    if (len <= kBlockRowMax) return 7;
+    return kGiant;
 }
 
 // ----------------------------------------------------------- device scan
@@ -120,8 +125,121 @@ static cudaError_t device_scan(const uint32_t* in, uint64_t n, uint64_t* out, ui
 
 // ----------------------------------------------------------- count / scatter
 
-__global__ void count_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
-                             const uint32_t* __restrict__ dst, uint32_t* __restrict__ cnt, IngestCtl* ctl) {
+// ------------------------------------------------ hot vertices (count, scatter)
+// A vertex that is an endpoint of a large share of the raw pairs (a hub)
+// would take one global atomic per pair in count and scatter, all on one
+// address.  A sample of the pairs names such vertices; count and scatter
+// then combine their increments per block in shared memory, and each block
+// writes a hub's entries into a range of the hub's row reserved for it (the
+// blocks' counts are prefix-summed per hub between the two passes).  Which
+// vertices are hot only changes speed, never the result.
+constexpr uint32_t kHotMax = 1024;          // hot vertices at most
+constexpr uint32_t kHotSlots = 2048;        // shared-memory hash of the hot ids
+constexpr uint32_t kSamplePairs = 32768;    // pairs sampled to find them
+constexpr uint32_t kSampleSlots = 4096;
+constexpr uint32_t kHotMinHits = 4;         // sample hits that make a vertex hot
+constexpr uint32_t kHotEmpty = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t hot_hash(uint32_t x) { return (x * 0x9E3779B1u) >> 21; }  // 11 bits
+
+// One block: count endpoint frequencies over a strided sample of the pairs.
+__global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
+                                                   const uint32_t* __restrict__ dst, uint32_t* __restrict__ hot_ids,
+                                                   uint32_t* __restrict__ hot_n) {
+    __shared__ uint32_t key[kSampleSlots];
+    __shared__ uint32_t cnt[kSampleSlots];
+    __shared__ uint32_t nsel;
+    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x) {
+        key[i] = kHotEmpty;
+        cnt[i] = 0;
+    }
+    if (threadIdx.x == 0) nsel = 0;
+    __syncthreads();
+    const uint64_t stride = m_raw > kSamplePairs ? m_raw / kSamplePairs : 1;
+    const uint64_t take = m_raw < kSamplePairs ? m_raw : kSamplePairs;
+    constexpr uint32_t kU = 8;  // pairs loaded per thread before any is counted
+    for (uint64_t k0 = threadIdx.x; k0 < take; k0 += (uint64_t)blockDim.x * kU) {
+        uint32_t e[2 * kU];
+#pragma unroll
+        for (uint32_t t = 0; t < kU; ++t) {
+            const uint64_t k = k0 + (uint64_t)t * blockDim.x;
+            e[2 * t] = e[2 * t + 1] = kHotEmpty;
+            if (k < take) {
+                e[2 * t] = src[k * stride];
+                e[2 * t + 1] = dst[k * stride];
+            }
+        }
+#pragma unroll
+        for (uint32_t t = 0; t < 2 * kU; ++t) {
+            const uint32_t x = e[t];
+            if (x >= n || e[t ^ 1u] == x) continue;  // out of range, padding or a loop
+            uint32_t h = (x * 0x9E3779B1u) >> 20;  // 12 bits
+            for (uint32_t probe = 0; probe < 8; ++probe, h = (h + 1) & (kSampleSlots - 1)) {
+                const uint32_t prev = atomicCAS(&key[h], kHotEmpty, x);
+                if (prev == kHotEmpty || prev == x) {
+                    atomicAdd(&cnt[h], 1u);
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x) {
+        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) {
+            const uint32_t at = atomicAdd(&nsel, 1u);
+            if (at < kHotMax) hot_ids[at] = key[i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *hot_n = min(nsel, kHotMax);
+}
+
+// Shared-memory table of the hot ids: slot -> (id, index in the hot list).
+struct HotTable {
+    uint32_t key[kHotSlots];
+    uint16_t idx[kHotSlots];
+    uint32_t local[kHotMax];  // this block's count or cursor per hot vertex
+};
+
+__device__ __forceinline__ void hot_build(HotTable& t, const uint32_t* hot_ids, uint32_t hot_n) {
+    for (uint32_t i = threadIdx.x; i < kHotSlots; i += blockDim.x) t.key[i] = kHotEmpty;
+    for (uint32_t i = threadIdx.x; i < kHotMax; i += blockDim.x) t.local[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < hot_n; i += blockDim.x) {
+        const uint32_t x = hot_ids[i];
+        uint32_t h = hot_hash(x);
+        while (true) {
+            if (atomicCAS(&t.key[h], kHotEmpty, x) == kHotEmpty) {
+                t.idx[h] = (uint16_t)i;
+                break;
+            }
+            h = (h + 1) & (kHotSlots - 1);
+        }
+    }
+    __syncthreads();
+}
+
+// index of x in the hot list, or -1
+__device__ __forceinline__ int hot_find(const HotTable& t, uint32_t x) {
+    uint32_t h = hot_hash(x);
+    while (true) {
+        const uint32_t k = t.key[h];
+        if (k == x) return t.idx[h];
+        if (k == kHotEmpty) return -1;
+        h = (h + 1) & (kHotSlots - 1);
+    }
+}
+
+// count: one per endpoint of every non-loop pair; hot endpoints are counted
+// in shared memory and also recorded per block (blk[block * kHotMax + h]).
+__global__ void __launch_bounds__(256) count_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
+                                                    const uint32_t* __restrict__ dst, uint32_t* __restrict__ cnt,
+                                                    const uint32_t* __restrict__ hot_ids,
+                                                    const uint32_t* __restrict__ hot_n_p, uint32_t* __restrict__ blk,
+                                                    IngestCtl* ctl) {
+    __shared__ HotTable t;
+    const uint32_t hot_n = *hot_n_p;
+    hot_build(t, hot_ids, hot_n);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_raw;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t u = src[i], v = dst[i];
@@ -130,20 +248,59 @@ __global__ void count_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restr
             continue;
         }
         if (u == v) continue;
-        atomicAdd(&cnt[u], 1u);
-        atomicAdd(&cnt[v], 1u);
+        int hu = hot_find(t, u), hv = hot_find(t, v);
+        if (hu >= 0) atomicAdd(&t.local[hu], 1u); else atomicAdd(&cnt[u], 1u);
+        if (hv >= 0) atomicAdd(&t.local[hv], 1u); else atomicAdd(&cnt[v], 1u);
+    }
+    __syncthreads();
+    for (uint32_t h = threadIdx.x; h < hot_n; h += blockDim.x) {
+        const uint32_t c = t.local[h];
+        blk[(uint64_t)blockIdx.x * kHotMax + h] = c;
+        if (c) atomicAdd(&cnt[hot_ids[h]], c);
     }
 }
 
-__global__ void scatter_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
-                               const uint32_t* __restrict__ dst, const uint64_t* __restrict__ start,
-                               uint32_t* __restrict__ fill, uint32_t* __restrict__ tmp) {
+// per hot vertex h: exclusive prefix of the blocks' counts -> each block's
+// first slot in the hub's row
+__global__ void __launch_bounds__(256) hot_block_bases(const uint32_t* __restrict__ hot_n_p, uint32_t nblk,
+                                                       uint32_t* __restrict__ blk) {
+    __shared__ uint32_t tmp[33];
+    const uint32_t h = blockIdx.x;
+    if (h >= *hot_n_p) return;
+    uint32_t carry = 0;
+    for (uint32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
+        const uint32_t b = b0 + threadIdx.x;
+        const uint32_t c = b < nblk ? blk[(uint64_t)b * kHotMax + h] : 0u;
+        uint32_t tot;
+        const uint32_t pre = block_excl_scan<uint32_t>(c, tmp, &tot);
+        if (b < nblk) blk[(uint64_t)b * kHotMax + h] = carry + pre;
+        carry += tot;
+    }
+}
+
+// scatter: each pair into both rows; hot rows at the block's reserved range
+// (same grid and pair-to-block assignment as count_kernel).
+__global__ void __launch_bounds__(256) scatter_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
+                                                      const uint32_t* __restrict__ dst,
+                                                      const uint64_t* __restrict__ start, uint32_t* __restrict__ fill,
+                                                      const uint32_t* __restrict__ hot_ids,
+                                                      const uint32_t* __restrict__ hot_n_p,
+                                                      const uint32_t* __restrict__ blk, uint32_t* __restrict__ tmp) {
+    __shared__ HotTable t;
+    const uint32_t hot_n = *hot_n_p;
+    hot_build(t, hot_ids, hot_n);
+    const uint32_t* myblk = blk + (uint64_t)blockIdx.x * kHotMax;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_raw;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t u = src[i], v = dst[i];
         if (u >= n || v >= n || u == v) continue;
-        tmp[start[u] + atomicAdd(&fill[u], 1u)] = v;
-        tmp[start[v] + atomicAdd(&fill[v], 1u)] = u;
+        const int hu = hot_find(t, u), hv = hot_find(t, v);
+        const uint64_t pu = hu >= 0 ? start[u] + myblk[hu] + atomicAdd(&t.local[hu], 1u)
+                                    : start[u] + atomicAdd(&fill[u], 1u);
+        const uint64_t pv = hv >= 0 ? start[v] + myblk[hv] + atomicAdd(&t.local[hv], 1u)
+                                    : start[v] + atomicAdd(&fill[v], 1u);
+        tmp[pu] = v;
+        tmp[pv] = u;
     }
 }
 
@@ -159,7 +316,7 @@ __global__ void classify_count(uint32_t n, const uint32_t* __restrict__ cnt, Ing
         uint32_t len = cnt[v];
         int k = row_class(len);
         if (k >= 0) atomicAdd(&c[k], 1u);
-        if (k == 6) atomicAdd(&giant, (unsigned long long)len);
+        if (k == kGiant) atomicAdd(&giant, (unsigned long long)len);
     }
     __syncthreads();
     if (threadIdx.x < kClasses && c[threadIdx.x]) atomicAdd(&ctl->cls_count[threadIdx.x], c[threadIdx.x]);
@@ -318,13 +475,14 @@ __global__ void __launch_bounds__(256) sort_warp_rows(const uint32_t* __restrict
 // sorts 1024 values in registers; merges with block size 2048..p2 run their
 // cross-warp steps (distance >= 1024) through shared memory and the rest in
 // registers.
+template <uint32_t kBlockWarps>
 __global__ void __launch_bounds__(kBlockWarps * 32) sort_block_rows(const uint32_t* __restrict__ list,
                                                                     uint32_t count,
                                                                     const uint64_t* __restrict__ start,
                                                                     const uint32_t* __restrict__ cnt,
                                                                     uint32_t* __restrict__ tmp,
                                                                     uint32_t* __restrict__ newlen) {
-    __shared__ uint32_t s[kBlockRowMax];
+    __shared__ uint32_t s[kBlockWarps * 1024];
     __shared__ uint32_t wlast[kBlockWarps];
     __shared__ uint32_t wcount[kBlockWarps];
     const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
@@ -502,15 +660,22 @@ __global__ void __launch_bounds__(256) giant_windows(const uint32_t* __restrict_
     }
 }
 
-__global__ void copy_rows(uint32_t n, const uint64_t* __restrict__ start, const uint32_t* __restrict__ tmp,
-                          const uint64_t* __restrict__ off, uint32_t* __restrict__ adj) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t v = gw; v < n; v += nw) {
-        uint64_t b = start[v], o = off[v], len = off[v + 1] - o;
-        for (uint64_t j = lane; j < len; j += 32) adj[o + j] = tmp[b + j];
-    }
+// adj[j] = tmp[start[v] + (j - off[v])] for every position j of row v: the
+// output positions are split evenly over the warps (rows of any length).
+__global__ void __launch_bounds__(256) copy_rows(uint32_t n, const uint64_t* __restrict__ start,
+                                                 const uint32_t* __restrict__ tmp, const uint64_t* __restrict__ off,
+                                                 uint32_t* __restrict__ adj) {
+    auto pre = [&](uint64_t) { return 0u; };
+    auto put = [&](const uint32_t* v, const uint64_t* j, const uint32_t*, uint32_t valid) {
+        uint32_t val[kWalkU];
+#pragma unroll
+        for (uint32_t t = 0; t < kWalkU; ++t)
+            if (valid >> t & 1u) val[t] = tmp[start[v[t]] + (j[t] - off[v[t]])];
+#pragma unroll
+        for (uint32_t t = 0; t < kWalkU; ++t)
+            if (valid >> t & 1u) adj[j[t]] = val[t];
+    };
+    walk_all_entries(off, n, pre, put);
 }
 
 // owner of each CSR entry (to ingest a CSR as raw pairs)
@@ -546,7 +711,20 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     DSG_TRY_CUDA(sc.get(&ctl, 1));
     DSG_TRY_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)n + 1) * 4, s));
     DSG_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IngestCtl), s));
-    { LaunchScope ls_("ingest_count_kernel", s); count_kernel<<<grid_for(m_raw, 256), 256, 0, s>>>(n, m_raw, src, dst, cnt, ctl); }
+    // count and scatter run on the same grid, so each block meets the same pairs
+    const uint32_t pair_grid = (uint32_t)std::min<uint64_t>((m_raw + 255) / 256 + 1, (uint64_t)dev_info().sms * 8);
+    uint32_t *hot_ids, *hot_n, *blk;
+    DSG_TRY_CUDA(sc.get(&hot_ids, kHotMax));
+    DSG_TRY_CUDA(sc.get(&hot_n, 1));
+    DSG_TRY_CUDA(sc.get(&blk, (size_t)pair_grid * kHotMax));
+    if (m_raw) {
+        { LaunchScope ls_("ingest_hot_sample", s); hot_sample<<<1, 1024, 0, s>>>(n, m_raw, src, dst, hot_ids, hot_n); }
+    } else {
+        DSG_TRY_CUDA(cudaMemsetAsync(hot_n, 0, 4, s));
+    }
+    { LaunchScope ls_("ingest_count_kernel", s); count_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, cnt, hot_ids, hot_n, blk, ctl); }
+    DSG_TRY_CUDA(cudaGetLastError());
+    { LaunchScope ls_("ingest_hot_bases", s); hot_block_bases<<<kHotMax, 256, 0, s>>>(hot_n, pair_grid, blk); }
     DSG_TRY_CUDA(cudaGetLastError());
     DSG_TRY_CUDA(device_scan(cnt, n, start, sums, s));
     { LaunchScope ls_("ingest_classify_count", s); classify_count<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, ctl); }
@@ -569,7 +747,7 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     DSG_TRY_CUDA(sc.get(&tmp, total ? total : 1));
     DSG_TRY_CUDA(sc.get(&lists.rows, nlist ? nlist : 1));
     DSG_TRY_CUDA(cudaMemsetAsync(newlen, 0, ((size_t)n + 1) * 4, s));  // reused as the fill counter
-    { LaunchScope ls_("ingest_scatter_kernel", s); scatter_kernel<<<grid_for(m_raw, 256), 256, 0, s>>>(n, m_raw, src, dst, start, newlen, tmp); }
+    { LaunchScope ls_("ingest_scatter_kernel", s); scatter_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, start, newlen, hot_ids, hot_n, blk, tmp); }
     DSG_TRY_CUDA(cudaGetLastError());
     {
         LaunchScope ls_("ingest_sort_small_rows", s);
@@ -584,16 +762,26 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     if (hc.cls_count[3]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<16><<<warp_grid(hc.cls_count[3]), 256, 0, s>>>(lists.rows + lists.base[3], hc.cls_count[3], start, cnt, tmp, newlen); }
     if (hc.cls_count[4]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<32><<<warp_grid(hc.cls_count[4]), 256, 0, s>>>(lists.rows + lists.base[4], hc.cls_count[4], start, cnt, tmp, newlen); }
     DSG_TRY_CUDA(cudaGetLastError());
+    // block rows: 2, 4 or 8 warps (each sorting 1024 values in registers) per row
     if (hc.cls_count[5]) {
         LaunchScope ls_("ingest_sort_block_rows", s);
-        uint32_t g = (uint32_t)std::min<uint64_t>(hc.cls_count[5], (uint64_t)sms * 4);
-        sort_block_rows<<<g, kBlockWarps * 32, 0, s>>>(lists.rows + lists.base[5], hc.cls_count[5], start, cnt, tmp,
-                                                       newlen);
+        uint32_t g = (uint32_t)std::min<uint64_t>(hc.cls_count[5], (uint64_t)sms * 16);
+        sort_block_rows<2><<<g, 64, 0, s>>>(lists.rows + lists.base[5], hc.cls_count[5], start, cnt, tmp, newlen);
+    }
+    if (hc.cls_count[6]) {
+        LaunchScope ls_("ingest_sort_block_rows", s);
+        uint32_t g = (uint32_t)std::min<uint64_t>(hc.cls_count[6], (uint64_t)sms * 8);
+        sort_block_rows<4><<<g, 128, 0, s>>>(lists.rows + lists.base[6], hc.cls_count[6], start, cnt, tmp, newlen);
+    }
+    if (hc.cls_count[7]) {
+        LaunchScope ls_("ingest_sort_block_rows", s);
+        uint32_t g = (uint32_t)std::min<uint64_t>(hc.cls_count[7], (uint64_t)sms * 4);
+        sort_block_rows<8><<<g, 256, 0, s>>>(lists.rows + lists.base[7], hc.cls_count[7], start, cnt, tmp, newlen);
     }
     DSG_TRY_CUDA(cudaGetLastError());
-    if (hc.cls_count[6]) {
-        const uint32_t ng = hc.cls_count[6];
-        const uint32_t* glist = lists.rows + lists.base[6];
+    if (hc.cls_count[kGiant]) {
+        const uint32_t ng = hc.cls_count[kGiant];
+        const uint32_t* glist = lists.rows + lists.base[kGiant];
         const uint32_t nwin = (uint32_t)(((uint64_t)n + kWin - 1) >> kWinBits);
         const uint64_t pairs = (uint64_t)ng * nwin;
         uint32_t *hist, *cursor, *ucnt, *spare;
@@ -632,7 +820,10 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = dev_alloc((void**)&g->adj, (size_t)(total2 ? total2 : 1) * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
-        { LaunchScope ls_("ingest_copy_rows", s); copy_rows<<<grid_for((uint64_t)n * 32, 256), 256, 0, s>>>(n, start, tmp, g->off, g->adj); }
+        if (total2) {
+            LaunchScope ls_("ingest_copy_rows", s);
+            copy_rows<<<(uint32_t)dev_info().sms * 8, 256, 0, s>>>(n, start, tmp, g->off, g->adj);
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
