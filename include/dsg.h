@@ -176,8 +176,8 @@ dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const uint32_t* 
 dsg_status dsg_kcore(const dsg_graph* g, uint32_t* out_core);
 
 /* As dsg_kcore, also writing up to nstats counters of the run into stats:
- *   [0] levels run (including skipped-to empty ones)
- *   [1] drain sub-rounds (grid-wide steps)
+ *   [0] levels run (one grid barrier each)
+ *   [1] row pieces queued to the level-wide work queue
  *   [2] remaining-list entries scanned (sum over levels)
  *   [3] remaining-list entries written (sum over levels)
  *   [4] degree atomics issued (decrements plus undos) */

@@ -281,7 +281,7 @@ class Graph:
         return out
 
     def kcore_counters(self, out=None):
-        """Core numbers plus the run's counters: levels, subrounds,
+        """Core numbers plus the run's counters: levels, pieces (queued row pieces),
         rem_scanned, rem_written, atomics."""
         if out is None:
             out = np.empty(max(self.n, 1), np.uint32)
@@ -289,7 +289,7 @@ class Graph:
         N.check(lib().dsg_kcore_stats(self._h, N.ptr(out), st.ctypes.data_as(N._U64P), 5), "kcore_stats")
         if isinstance(out, np.ndarray):
             out = out[:self.n]
-        keys = ("levels", "subrounds", "rem_scanned", "rem_written", "atomics")
+        keys = ("levels", "pieces", "rem_scanned", "rem_written", "atomics")
         return out, {k: int(v) for k, v in zip(keys, st)}
 
 

@@ -80,7 +80,7 @@ struct HistShared {
     uint32_t he[kShBins];
 };
 
-__global__ void __launch_bounds__(kHistTB) core_hist_kernel(const uint64_t* __restrict__ off,
+__global__ void __launch_bounds__(kHistTB, 3) core_hist_kernel(const uint64_t* __restrict__ off,
                                                              const uint32_t* __restrict__ adj,
                                                              const uint32_t* __restrict__ core, uint32_t n,
                                                              const CbdsCtl* __restrict__ ctl,

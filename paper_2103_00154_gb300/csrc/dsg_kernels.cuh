@@ -8,6 +8,18 @@
 
 namespace dsg {
 
+// Adjacency entries are read once per solve: load them with the streaming
+// (evict-first) policy so they do not push the per-vertex state (degrees,
+// marks), which every entry looks up at random, out of L2.
+// (DSG_PLAIN_ADJ_LOADS builds the plain-load variant, for comparison.)
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
+#ifdef DSG_PLAIN_ADJ_LOADS
+    return *p;
+#else
+    return __ldcs(p);
+#endif
+}
+
 // Tuning knobs of the round kernels (see tune.cu for the defaults and the
 // autotuner that picks them).
 struct Tuning {
@@ -189,7 +201,7 @@ __device__ __forceinline__ void scan_block_list(const uint64_t* __restrict__ off
                         uint32_t mid = (a + z) >> 1;
                         if (sm.start[mid] <= e) a = mid; else z = mid;
                     }
-                    bu[j] = adj[sm.beg[a] + (e - sm.start[a])];
+                    bu[j] = ld_stream(adj + sm.beg[a] + (e - sm.start[a]));
                     bv[j] = sm.v[a];
                     valid |= 1u << j;
                 }
@@ -235,7 +247,7 @@ __device__ __forceinline__ void scan_block_rows(const uint32_t* __restrict__ adj
                         const uint32_t mid = (a + z) >> 1;
                         if (sm.start[mid] <= e) a = mid; else z = mid;
                     }
-                    bu[j] = adj[sm.beg[a] + (e - sm.start[a])];
+                    bu[j] = ld_stream(adj + sm.beg[a] + (e - sm.start[a]));
                     bv[j] = sm.v[a];
                     valid |= 1u << j;
                 }
@@ -408,7 +420,7 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
 #ifdef DSG_DEBUG_BOUNDS
                     if (pos >= off[dbg_n]) { bu[j] = 0xffffffffu; bv[j] = 0xffffffffu; valid |= 1u << j; continue; }
 #endif
-                    bu[j] = adj[pos];
+                    bu[j] = ld_stream(adj + pos);
                     valid |= 1u << j;
                 }
             }
@@ -439,7 +451,7 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
                 bu[j] = 0;
                 bv[j] = v;
                 if (jj < end) {
-                    bu[j] = adj[jj];
+                    bu[j] = ld_stream(adj + jj);
                     valid |= 1u << j;
                 }
             }

@@ -1,36 +1,44 @@
 // Core numbers by the level-synchronous peel of Algorithm 2's first phase
-// (PKC), as one persistent cooperative kernel.
+// (PKC), as one persistent cooperative kernel with one grid barrier per level.
 //
-// Level k (Alg. 2 first phase), in sub-rounds separated by grid barriers:
-//   sub-round 0 scans the remaining vertices: degree <= k joins the level's
-//     frontier (Alg. 2 "if v.deg = k: buff[end++] <- v"), degree > k stays in
-//     the (compacted) remaining list; each block then drains the vertices it
-//     found itself: for every frontier vertex v and neighbour u with
-//     deg[u] > k, a = atomicSub(deg[u], 1); a == k+1 puts u in the frontier
-//     (it just reached k); a <= k is undone with atomicAdd (another thread got
-//     there first) -- Alg. 2's drain loop;
-//   later sub-rounds drain the vertices that reached k and did not fit the
-//     finding block's own queue;
-//   the level ends when a sub-round adds nothing; "visited" grows by the
-//   frontier size (Alg. 2 "atomicAdd(visited, end)").
-// Scanning and draining share sub-round 0, so a level with no cascade costs
-// one grid barrier.  Because other blocks' drains run while a block scans, a
-// vertex is taken into a frontier by claiming its bit in a bitmap (atomicOr):
-// whichever of the scan and the drain that brought it to k claims it first
-// drains it, exactly once.  A scanned degree below k can only be such a
-// vertex caught between a decrement and its undo: every vertex whose degree
-// was below k at the level's start was claimed at an earlier level.
+// Level k (Alg. 2 first phase):
+//   scan: every block walks its own segment of the remaining vertices; degree
+//     <= k joins the level's frontier (Alg. 2 "if v.deg = k: buff[end++] <-
+//     v"), degree > k stays in the (compacted) segment;
+//   drain: for every frontier vertex v and neighbour u with deg[u] > k,
+//     a = atomicSub(deg[u], 1); a == k+1 puts u in the frontier (it just
+//     reached k); a <= k is undone with atomicAdd (another thread got there
+//     first) -- Alg. 2's drain loop.  A block drains the rows its scan found
+//     (up to inline_max entries each) and the vertices that reach k while it
+//     drains (rows up to local_max entries, while its local budget lasts:
+//     PKC's thread-local buffer); everything else goes to a level-wide queue
+//     of row pieces (at most chunk_len entries each) that blocks with no
+//     work of their own take from as it comes, so neither hub rows nor
+//     cascades that outgrow one block cost an extra grid barrier;
+//   the level ends when the queue is drained and no block can add to it: a
+//     counter holds one token per block (given back when its scan and own
+//     draining are done) plus one per queued piece (given back once the piece
+//     and everything it led the block to do locally are done), and the level
+//     is over when it reaches zero;
+//   "visited" grows by the frontier size (Alg. 2 "atomicAdd(visited, end)").
+// Scan and drain overlap, so a vertex is taken into the frontier by claiming
+// its bit in a bitmap (atomicOr): whichever of the scan and the decrement that
+// brought it to k claims it first drains it, exactly once.  A scanned degree
+// below k can only be such a vertex caught between a decrement and its undo:
+// every vertex whose degree was below k at the level's start was claimed at an
+// earlier level.
 // Empty levels are skipped: the next k is the least degree above k seen by the
 // scan and by every decrement of the level (the last value each vertex takes
 // is among them, so no level with work is skipped).
 // When visited == n, deg[v] is the core number of v.
 //
-// Counters that blocks read after a barrier (frontier sizes, claims, the
-// remaining-list cursor, the least degree) live in a ring of three slots
-// indexed by the sub-round: sub-round j adds into slot j % 3, every block
-// reads it after barrier j, and block 0 clears slot (j + 1) % 3 during
-// sub-round j -- after every block has read it (two barriers earlier) and
-// before anyone adds into it (after barrier j).
+// Per-level counters (queue tail, the token count, claims, least
+// degree) sit in a ring of three sets, level L using set L % 3: blocks read a
+// level's claims and least degree right after its barrier, so block 0 re-arms
+// set (L+1) % 3 at the start of level L -- two barriers after that set's
+// last reads, one barrier before its next use.  Queue slots are reused by
+// every level; a slot is published by writing the level's tag (level + 1)
+// after its contents, so a stale slot is never taken for a new one.
 #include <string.h>
 
 #include <cooperative_groups.h>
@@ -42,12 +50,14 @@ namespace cg = cooperative_groups;
 
 namespace dsg {
 
-struct __align__(128) CoreSlot {
-    unsigned long long qcnt;    // drain-frontier short rows pushed
-    unsigned long long ccnt;    // chunk items pushed
-    unsigned long long pushed;  // vertices claimed
-    uint32_t nmin;              // least degree above k seen
-    uint32_t pad[25];
+struct __align__(128) CoreLevel {
+    unsigned long long pending;  // block tokens + queued pieces not yet drained
+    unsigned long long pad0[15];
+    unsigned long long tail;     // next queue slot a producer fills
+    unsigned long long pad2[15];
+    unsigned long long claimed;  // vertices claimed at this level
+    uint32_t nmin;               // least degree above k seen
+    uint32_t pad3[29];
 };
 
 struct __align__(128) CoreCtl {
@@ -57,11 +67,11 @@ struct __align__(128) CoreCtl {
     uint32_t pad1[31];
     uint32_t init_min;
     uint32_t pad2[31];
-    CoreSlot slot[3];
-    unsigned long long atomics;  // degree atomics (decrements + undos), never read in the kernel
-    unsigned long long pad3[15];
-    unsigned long long rem_scanned, rem_written;  // statistics, summed by every block
-    unsigned long long levels, subrounds;
+    CoreLevel lvl[3];
+    unsigned long long atomics;  // statistics, summed by every block, never read in the kernel
+    unsigned long long rem_scanned, rem_written, pieces;
+    unsigned long long pad3[12];
+    unsigned long long levels;
     unsigned long long dbg[4];   // bounds-check builds: first bad access (site, index, capacity, level)
     unsigned long long stamps;
 };
@@ -97,29 +107,29 @@ struct CoreArgs {
     uint64_t* QB;     // ... their row starts
     uint32_t* QL;     // ... and row lengths
     uint64_t seg;     // segment length per block
-    uint32_t* Q;      // drain frontier (short rows), all levels ...
-    uint64_t* QgB;    // ... their row starts
-    uint32_t* QgL;    // ... and row lengths
-    uint64_t* C;      // chunk items (long rows), all levels
+    uint32_t* IV;     // level queue (cap slots) of row pieces: row owner ...
+    uint64_t* IB;     // ... first entry
+    uint32_t* IL;     // ... entries (<= chunk_len)
+    uint32_t* IR;     // ... publication tag (level + 1)
+    uint64_t cap;
     CoreCtl* ctl;
     uint64_t limit_ns;
-    uint32_t short_max;
     uint32_t chunk_len;
     uint32_t hot_deg;
     uint32_t local_max;   // rows up to this length found while draining stay in the block
-    uint32_t local_work;  // ... while the block's local entries this sub-round stay within this
-    uint32_t inline_max;  // rows up to this length claimed by a block's scan may be drained by that block
-    uint64_t chunk_cap;
+    uint32_t local_work;  // ... while the block's local entries per batch stay within this
+    uint32_t inline_max;  // rows up to this length claimed by a block's scan are drained by that block
     uint64_t* trace;      // nullable: block 0 stamps (%globaltimer, kind) after every barrier
     uint64_t trace_cap;
 };
 
 // Block-local frontier: vertices that reach k while this block drains are
-// drained by the same block in the same sub-round (PKC's thread-local buff,
-// Algorithm 2), so a chain of degree-k vertices costs no grid barrier per
-// link.  Overflow goes to the global frontier of the next sub-round.
+// drained by the same block (PKC's thread-local buff, Algorithm 2), so a
+// chain of degree-k vertices costs no queue round trip per link.
 template <int TB>
 constexpr uint32_t local_q_cap() { return TB >= 1024 ? 640 : 1024; }
+
+constexpr uint32_t kTakeSlots = 8;  // queue slots a block takes at a time
 
 template <int TB>
 struct CoreSmem {
@@ -131,13 +141,16 @@ struct CoreSmem {
     uint64_t lqb[kLocalQ];  // ... their row starts
     uint32_t lql[kLocalQ];  // ... and row lengths
     uint32_t lq_tail;
-    uint32_t lq_work;  // row entries this block has taken on locally in this sub-round
-    uint32_t own;      // vertices this block's scan claimed in this sub-round
-    uint32_t kept;     // vertices this block's scan kept
-    uint32_t acc_min;  // block reductions at the end of a sub-round
-    unsigned long long acc_pushed, acc_atomics;
-    uint64_t bases[4];
-    uint64_t red[33];
+    uint32_t lq_work;       // row entries this block has taken on locally in this batch
+    uint32_t own;           // vertices this block's scan claimed
+    uint32_t kept;          // vertices this block's scan kept
+    uint32_t tv[kTakeSlots];  // queue pieces taken: row owner ...
+    uint64_t tb[kTakeSlots];  // ... first entry
+    uint32_t tl[kTakeSlots];  // ... entries
+    uint32_t tcount;
+    uint32_t flag;
+    uint32_t acc_min;       // block reductions at the end of a level
+    unsigned long long acc_claimed, acc_atomics, acc_pieces;
     uint32_t redm[33];
 };
 
@@ -147,29 +160,42 @@ __device__ __forceinline__ bool claim_vertex(uint32_t* claim, uint32_t v) {
     return !(atomicOr(&claim[v >> 5], bit) & bit);
 }
 
-// Put v (row start beg, length len) into the drain frontier of the next
-// sub-round: short rows by id (with start and length) into Q, long rows as
-// chunk items into C, at positions after the items of earlier sub-rounds
-// (qbase / cbase) counted in slot S.  Called by any subset of lanes; short
-// pushes are aggregated over the lanes that take this path together.
-__device__ __forceinline__ void push_frontier(const CoreArgs& a, CoreSlot* S, uint64_t qbase, uint64_t cbase,
-                                              uint32_t v, uint64_t beg, uint64_t len, uint32_t short_max) {
-    if (len <= short_max) {
-        cg::coalesced_group g = cg::coalesced_threads();
-        unsigned long long base = 0;
-        if (g.thread_rank() == 0) base = atomicAdd(&S->qcnt, (unsigned long long)g.size());
-        base = g.shfl(base, 0);
-        const uint64_t at = qbase + base + g.thread_rank();
-        DSG_BOUND(a.ctl, 1, at, a.n, 0, return);
-        a.Q[at] = v;
-        a.QgB[at] = beg;
-        a.QgL[at] = (uint32_t)len;
-    } else {
-        uint64_t nch = (len + a.chunk_len - 1) / a.chunk_len;
-        unsigned long long c0 = atomicAdd(&S->ccnt, (unsigned long long)nch);
-        DSG_BOUND(a.ctl, 2, cbase + c0 + nch - 1, a.chunk_cap, 0, return);
-        for (uint64_t c = 0; c < nch; ++c) a.C[cbase + c0 + c] = ((uint64_t)v << 32) | c;
+// Queue the row of v (start beg, len entries) as pieces of at most chunk_len
+// entries for the level counted in P (tag = level + 1).  The token count is
+// raised before a piece can be seen.  Called by any subset of lanes; the
+// counters are updated once per group of lanes that call together.
+__device__ __forceinline__ uint64_t queue_row(const CoreArgs& a, CoreLevel* P, uint32_t tag, uint32_t v,
+                                              uint64_t beg, uint64_t len) {
+    const uint64_t np = (len + a.chunk_len - 1) / a.chunk_len;
+    cg::coalesced_group g = cg::coalesced_threads();
+    uint64_t pre = np;  // inclusive prefix of the group's piece counts
+    for (uint32_t o = 1; o < g.size(); o <<= 1) {
+        const uint64_t t = g.shfl_up(pre, o);
+        if (g.thread_rank() >= o) pre += t;
     }
+    const uint64_t total = g.shfl(pre, g.size() - 1);
+    pre -= np;
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0 && total) {
+        atomicAdd(&P->pending, (unsigned long long)total);
+        base = atomicAdd(&P->tail, (unsigned long long)total);
+    }
+    base = g.shfl(base, 0);
+    const uint64_t s0 = base + pre;
+    for (uint64_t c = 0; c < np; ++c) {
+        const uint64_t at = s0 + c;
+        DSG_BOUND(a.ctl, 1, at, a.cap, tag, break);
+        a.IV[at] = v;
+        a.IB[at] = beg + c * a.chunk_len;
+        a.IL[at] = (uint32_t)min((uint64_t)a.chunk_len, len - c * a.chunk_len);
+    }
+    __threadfence();
+    for (uint64_t c = 0; c < np; ++c) {
+        const uint64_t at = s0 + c;
+        DSG_BOUND(a.ctl, 6, at, a.cap, tag, break);
+        st_release_u32(&a.IR[at], tag);
+    }
+    return np;
 }
 
 template <int TB>
@@ -177,9 +203,10 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
     __shared__ CoreSmem<TB> sm;
     CoreCtl* ctl = a.ctl;
     const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31u;
     const uint32_t n = a.n;
     uint64_t nstamp = 0;
-    // trace entries: 2 words each, (time, kind << 32 | k); kind 0 start, 1 init, 2 scan sub-round, 3 drain
+    // trace entries: 2 words each, (time, kind << 32 | k); kind 0 start, 1 init, 2 level
     auto stamp = [&](uint32_t kind, uint32_t kk) {
         if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 1 < a.trace_cap) {
             a.trace[2 * nstamp] = global_ns();
@@ -216,187 +243,102 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
     uint32_t* const myQA = a.QA + segoff;
     uint64_t* const myQB = a.QB + segoff;
     uint32_t* const myQL = a.QL + segoff;
-    uint64_t qpos = 0, cpos = 0, qlo = 0, qhi = 0, clo = 0, chi = 0;
-    uint64_t visited = 0, j = 0;
-    uint64_t level = 0, subrounds = 0;
+    uint64_t visited = 0, level = 0;
     uint32_t* deg = a.deg;
     for (;;) {
-        uint32_t level_min = 0xffffffffu;
-        uint64_t my_n_next = 0;
-        for (bool first = true;; first = false) {
-            CoreSlot* S = &ctl->slot[j % 3];
-            if (blockIdx.x == 0 && tid == 0) {
-                CoreSlot* R = &ctl->slot[(j + 1) % 3];
-                R->qcnt = 0;
-                R->ccnt = 0;
-                R->pushed = 0;
-                R->nmin = 0xffffffffu;
-            }
-            uint32_t dmn = 0xffffffffu;
-            uint64_t dpushed = 0, natom = 0;
-            // u reached k: drain it in this block if there is room, else globally
-            auto reach_k = [&](uint32_t u) {
-                // the decrement that brought u to k is unique; only a scan of the
-                // same sub-round can also see u at k, so only there is the bit raced for
-                if (first) {
-                    if (!claim_vertex(a.claim, u)) return;  // the scan took it
-                } else {
-                    atomicOr(&a.claim[u >> 5], 1u << (u & 31u));
-                }
-                const uint64_t beg = a.off[u];
-                const uint64_t len = a.off[u + 1] - beg;
-                ++dpushed;
-                // keep it in the block while the block's own share stays small:
-                // past local_work entries a grid-wide sub-round is cheaper
-                if (len <= a.local_max && atomicAdd(&sm.lq_work, (uint32_t)len) + len <= a.local_work) {
-                    uint32_t pos = atomicAdd(&sm.lq_tail, 1u);
-                    if (pos < CoreSmem<TB>::kLocalQ) {
-                        sm.lq[pos] = u;
-                        sm.lqb[pos] = beg;
-                        sm.lql[pos] = (uint32_t)len;
-                        return;
-                    }
-                }
-                push_frontier(a, S, qpos, cpos, u, beg, len, a.short_max);
-            };
-            // c was just taken from u's degree, which was old: keep what brings
-            // it down to k, give back the rest (Algorithm 2's undo, for c units),
-            // and report the crossing into k
-            auto settle = [&](uint32_t u, uint32_t old, uint32_t c) {
-                if (old <= k) {
-                    atomicAdd(&deg[u], c);
-                    ++natom;
+        const uint32_t tag = (uint32_t)(level + 1);
+        CoreLevel* P = &ctl->lvl[level % 3];
+        if (blockIdx.x == 0 && tid == 0) {
+            CoreLevel* R = &ctl->lvl[(level + 1) % 3];  // last read two barriers ago, next used after this level
+            R->pending = gridDim.x;
+            R->tail = 0;
+            R->claimed = 0;
+            R->nmin = 0xffffffffu;
+        }
+        uint32_t dmn = 0xffffffffu;
+        uint64_t claimed = 0, natom = 0, npieces = 0;
+        // u reached k: drain it in this block if there is room, else queue it
+        // (a scan still running elsewhere may have taken it first)
+        auto reach_k = [&](uint32_t u) {
+            if (!claim_vertex(a.claim, u)) return;
+            ++claimed;
+            const uint64_t beg = a.off[u];
+            const uint64_t len = a.off[u + 1] - beg;
+            if (len <= a.local_max && atomicAdd(&sm.lq_work, (uint32_t)len) + len <= a.local_work) {
+                uint32_t pos = atomicAdd(&sm.lq_tail, 1u);
+                if (pos < CoreSmem<TB>::kLocalQ) {
+                    sm.lq[pos] = u;
+                    sm.lqb[pos] = beg;
+                    sm.lql[pos] = (uint32_t)len;
                     return;
                 }
-                uint32_t legit = min(c, old - k);
-                if (legit < c) {
-                    atomicAdd(&deg[u], c - legit);
-                    ++natom;
-                }
-                uint32_t nv = old - legit;
-                if (nv == k) reach_k(u);
-                else dmn = min(dmn, nv);
-            };
-            auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
-                uint32_t d[kBatch], old[kBatch], need = 0;
+            }
+            if (len) npieces += queue_row(a, P, tag, u, beg, len);
+        };
+        // c was just taken from u's degree, which was old: keep what brings
+        // it down to k, give back the rest (Algorithm 2's undo, for c units),
+        // and report the crossing into k
+        auto settle = [&](uint32_t u, uint32_t old, uint32_t c) {
+            if (old <= k) {
+                atomicAdd(&deg[u], c);
+                ++natom;
+                return;
+            }
+            uint32_t legit = min(c, old - k);
+            if (legit < c) {
+                atomicAdd(&deg[u], c - legit);
+                ++natom;
+            }
+            uint32_t nv = old - legit;
+            if (nv == k) reach_k(u);
+            else dmn = min(dmn, nv);
+        };
+        auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
+            uint32_t d[kBatch], old[kBatch], need = 0;
 #pragma unroll
-                for (uint32_t jj = 0; jj < kBatch; ++jj) {
-                    if (!(valid >> jj & 1u)) continue;
+            for (uint32_t jj = 0; jj < kBatch; ++jj) {
+                if (!(valid >> jj & 1u)) continue;
 #ifdef DSG_DEBUG_BOUNDS
-                    if (u[jj] >= n) {
-                        DSG_BOUND(ctl, 4, u[jj], n, level, (void)0);
-                        continue;
-                    }
+                if (u[jj] >= n) {
+                    DSG_BOUND(ctl, 4, u[jj], n, level, (void)0);
+                    continue;
+                }
 #endif
-                    if (u[jj] == v[jj]) continue;
-                    d[jj] = deg[u[jj]];
-                    need |= 1u << jj;
-                }
+                if (u[jj] == v[jj]) continue;
+                d[jj] = deg[u[jj]];
+                need |= 1u << jj;
+            }
 #pragma unroll
-                for (uint32_t jj = 0; jj < kBatch; ++jj) {
-                    if (!(need >> jj & 1u)) continue;
-                    if (d[jj] <= k || (d[jj] >= hot && agg_add(sm.agg, u[jj]))) {
-                        need &= ~(1u << jj);  // already at k, or settled at the flush
-                        continue;
-                    }
-                    old[jj] = atomicSub(&deg[u[jj]], 1u);
+            for (uint32_t jj = 0; jj < kBatch; ++jj) {
+                if (!(need >> jj & 1u)) continue;
+                if (d[jj] <= k || (d[jj] >= hot && agg_add(sm.agg, u[jj]))) {
+                    need &= ~(1u << jj);  // already at k, or settled at the flush
+                    continue;
+                }
+                old[jj] = atomicSub(&deg[u[jj]], 1u);
+                ++natom;
+            }
+#pragma unroll
+            for (uint32_t jj = 0; jj < kBatch; ++jj)
+                if (need >> jj & 1u) settle(u[jj], old[jj], 1u);
+        };
+        auto flush = [&]() {
+            __syncthreads();
+            for (uint32_t i = tid; i < kAggSlots; i += TB) {
+                uint32_t key = sm.agg.key[i];
+                if (key != kAggEmpty) {
+                    uint32_t c = sm.agg.cnt[i];
+                    sm.agg.key[i] = kAggEmpty;
+                    sm.agg.cnt[i] = 0;
+                    uint32_t old = atomicSub(&deg[key], c);
                     ++natom;
+                    settle(key, old, c);
                 }
-#pragma unroll
-                for (uint32_t jj = 0; jj < kBatch; ++jj)
-                    if (need >> jj & 1u) settle(u[jj], old[jj], 1u);
-            };
-            auto flush = [&]() {
-                __syncthreads();
-                for (uint32_t i = tid; i < kAggSlots; i += TB) {
-                    uint32_t key = sm.agg.key[i];
-                    if (key != kAggEmpty) {
-                        uint32_t c = sm.agg.cnt[i];
-                        sm.agg.key[i] = kAggEmpty;
-                        sm.agg.cnt[i] = 0;
-                        uint32_t old = atomicSub(&deg[key], c);
-                        ++natom;
-                        settle(key, old, c);
-                    }
-                }
-                __syncthreads();
-            };
-            if (tid == 0) {
-                sm.lq_tail = 0;
-                sm.lq_work = 0;
-                sm.own = 0;
-                sm.kept = 0;
-                sm.acc_min = 0xffffffffu;
-                sm.acc_pushed = 0;
-                sm.acc_atomics = 0;
             }
             __syncthreads();
-            if (first) {
-                // ---- scan: claim degree <= k, keep degree > k, drop the claimed
-                uint32_t mn = 0xffffffffu;
-                const uint64_t lim = my_rem ? my_n : n;
-                const uint64_t stride = my_rem ? TB : (uint64_t)gridDim.x * TB;
-                uint64_t scanned = 0;
-                for (uint64_t t = my_rem ? 0 : (uint64_t)blockIdx.x * TB; t < lim; t += stride) {
-                    const uint64_t i = t + tid;
-                    bool keep = false;
-                    uint32_t v = 0;
-                    if (i < lim) {
-                        ++scanned;
-                        v = my_rem ? my_rem[i] : (uint32_t)i;
-                        const uint32_t dv = deg[v];
-                        const uint32_t taken = a.claim[v >> 5] >> (v & 31u) & 1u;
-                        if (!taken) {
-                            if (dv > k) {
-                                keep = true;
-                                mn = min(mn, dv);
-                            } else if (claim_vertex(a.claim, v)) {
-                                ++dpushed;
-                                const uint64_t beg = a.off[v];
-                                const uint64_t len = a.off[v + 1] - beg;
-                                // drained by this block, or, for rows above inline_max,
-                                // spread over every warp in the next sub-round
-                                if (len <= a.inline_max) {
-                                    uint32_t pos = atomicAdd(&sm.own, 1u);
-                                    DSG_BOUND(ctl, 5, pos, a.seg, level, pos = 0);
-                                    myQA[pos] = v;
-                                    myQB[pos] = beg;
-                                    myQL[pos] = (uint32_t)len;
-                                } else {
-                                    push_frontier(a, S, qpos, cpos, v, beg, len, a.short_max);
-                                }
-                            }
-                        }
-                    }
-                    // keep: warp ballot, one shared-memory atomic per warp
-                    const uint32_t bal = __ballot_sync(kFullMask, keep);
-                    uint32_t base = 0;
-                    if ((tid & 31u) == 0 && bal) base = atomicAdd(&sm.kept, (uint32_t)__popc(bal));
-                    base = __shfl_sync(kFullMask, base, 0);
-                    if (keep) {
-                        uint64_t at = base + __popc(bal & lanemask_lt());
-                        DSG_BOUND(ctl, 3, at, a.seg, level, keep = false);
-                        if (keep) my_rem_next[at] = v;
-                    }
-                }
-                dmn = min(dmn, mn);
-                __syncthreads();
-                // ---- drain what this block's scan claimed
-                const uint32_t own = (uint32_t)min((uint64_t)sm.own, a.seg);
-                my_n_next = sm.kept;
-                {
-                    const uint64_t bs = block_sum<uint64_t>(scanned, sm.red);
-                    if (tid == 0) {
-                        atomicAdd(&ctl->rem_scanned, (unsigned long long)bs);
-                        atomicAdd(&ctl->rem_written, (unsigned long long)my_n_next);
-                    }
-                }
-                scan_block_rows<TB>(a.adj, myQA, myQB, myQL, own, sm.btile, visit);
-            } else {
-                scan_frontier<TB>(a.off, a.adj, a.Q, qlo, qhi, a.C, clo, chi, a.chunk_len, visit, n, a.QgB, a.QgL);
-            }
-            flush();
-            // drain what this block found, until it finds nothing more
+        };
+        // drain what this block found, until it finds nothing more
+        auto local_loop = [&]() {
             for (uint32_t lq_lo = 0;;) {
                 uint32_t lq_hi = min(sm.lq_tail, CoreSmem<TB>::kLocalQ);
                 __syncthreads();
@@ -406,38 +348,181 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                 flush();
                 lq_lo = lq_hi;
             }
-            // block reductions: warp shuffles, one shared atomic per warp, then
-            // thread 0 adds the block's totals (the barrier synchronises first)
-            dmn = warp_min(dmn);
-            dpushed = warp_sum(dpushed);
-            natom = warp_sum(natom);
-            if ((tid & 31u) == 0) {
-                if (dmn != 0xffffffffu) atomicMin(&sm.acc_min, dmn);
-                if (dpushed) atomicAdd(&sm.acc_pushed, (unsigned long long)dpushed);
-                if (natom) atomicAdd(&sm.acc_atomics, (unsigned long long)natom);
+        };
+        if (tid == 0) {
+            sm.lq_tail = 0;
+            sm.lq_work = 0;
+            sm.own = 0;
+            sm.kept = 0;
+            sm.acc_min = 0xffffffffu;
+            sm.acc_claimed = 0;
+            sm.acc_atomics = 0;
+            sm.acc_pieces = 0;
+        }
+        __syncthreads();
+        // ---- scan: claim degree <= k, keep degree > k, drop the claimed
+        {
+            uint32_t mn = 0xffffffffu;
+            const uint64_t lim = my_rem ? my_n : n;
+            const uint64_t stride = my_rem ? TB : (uint64_t)gridDim.x * TB;
+            uint64_t scanned = 0;
+            for (uint64_t t = my_rem ? 0 : (uint64_t)blockIdx.x * TB; t < lim; t += stride) {
+                const uint64_t i = t + tid;
+                bool keep = false;
+                uint32_t v = 0;
+                if (i < lim) {
+                    ++scanned;
+                    v = my_rem ? my_rem[i] : (uint32_t)i;
+                    const uint32_t dv = deg[v];
+                    const uint32_t taken = a.claim[v >> 5] >> (v & 31u) & 1u;
+                    if (!taken) {
+                        if (dv > k) {
+                            keep = true;
+                            mn = min(mn, dv);
+                        } else if (claim_vertex(a.claim, v)) {
+                            ++claimed;
+                            const uint64_t beg = a.off[v];
+                            const uint64_t len = a.off[v + 1] - beg;
+                            // drained by this block, or, for rows above inline_max,
+                            // queued in pieces for every block
+                            if (len <= a.inline_max) {
+                                uint32_t pos = atomicAdd(&sm.own, 1u);
+                                DSG_BOUND(ctl, 5, pos, a.seg, level, pos = 0);
+                                myQA[pos] = v;
+                                myQB[pos] = beg;
+                                myQL[pos] = (uint32_t)len;
+                            } else {
+                                npieces += queue_row(a, P, tag, v, beg, len);
+                            }
+                        }
+                    }
+                }
+                // keep: warp ballot, one shared-memory atomic per warp
+                const uint32_t bal = __ballot_sync(kFullMask, keep);
+                uint32_t base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&sm.kept, (uint32_t)__popc(bal));
+                base = __shfl_sync(kFullMask, base, 0);
+                if (keep) {
+                    uint64_t at = base + __popc(bal & lanemask_lt());
+                    DSG_BOUND(ctl, 3, at, a.seg, level, keep = false);
+                    if (keep) my_rem_next[at] = v;
+                }
+            }
+            dmn = min(dmn, mn);
+            scanned = warp_sum(scanned);
+            if (lane == 0 && scanned) atomicAdd(&ctl->rem_scanned, (unsigned long long)scanned);
+        }
+        __syncthreads();
+        // ---- drain what this block's scan claimed, and what that leads to locally
+        {
+            const uint32_t own = (uint32_t)min((uint64_t)sm.own, a.seg);
+            scan_block_rows<TB>(a.adj, myQA, myQB, myQL, own, sm.btile, visit);
+            flush();
+            local_loop();
+        }
+        // the block adds nothing more except from queue pieces: give back its token
+        __syncthreads();
+        if (tid == 0) atomicAdd(&P->pending, ~0ull);  // minus one
+        // ---- take queue pieces until the level has none left and no block can add any.
+        // Slot s belongs to block s mod grid, so consecutive pieces go to
+        // different blocks; a block takes its next kTakeSlots slots at a time.
+        for (uint64_t round = 0;; round += kTakeSlots) {
+            if (tid == 0) {
+                sm.flag = 0;
+                if (ld_volatile_u64((const uint64_t*)&P->pending) == 0 || (ld_volatile_u32(&ctl->err) & ERR_TIMEOUT)) sm.flag = 1;
             }
             __syncthreads();
-            if (tid == 0) {
-                if (sm.acc_min != 0xffffffffu) atomicMin(&S->nmin, sm.acc_min);
-                if (sm.acc_pushed) atomicAdd(&S->pushed, sm.acc_pushed);
-                if (sm.acc_atomics) atomicAdd(&ctl->atomics, sm.acc_atomics);
+            if (sm.flag) break;
+            const uint64_t slot = (uint64_t)blockIdx.x + (round + tid) * gridDim.x;
+            bool todo = tid < kTakeSlots && slot < a.cap;
+            if (!__syncthreads_or(todo)) {
+                // past the queue's capacity: nothing more can come to this block
+                if (tid == 0) {
+                    const uint64_t w0 = global_ns();
+                    while (ld_volatile_u64((const uint64_t*)&P->pending) != 0) {
+                        if (global_ns() - w0 > a.limit_ns || (ld_volatile_u32(&ctl->err) & ERR_TIMEOUT)) {
+                            atomicOr(&ctl->err, ERR_TIMEOUT);
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+                __syncthreads();
+                break;
             }
-            if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
-            stamp(first ? 2 : 3, k);
-            ++subrounds;
-            const uint64_t qcnt = ld_relaxed_u64(&S->qcnt);
-            const uint64_t ccnt = ld_relaxed_u64(&S->ccnt);
-            visited += ld_relaxed_u64(&S->pushed);
-            level_min = min(level_min, ld_relaxed_u32(&S->nmin));
-            qlo = qpos;
-            qhi = qpos + qcnt;
-            qpos = qhi;
-            clo = cpos;
-            chi = cpos + ccnt;
-            cpos = chi;
-            ++j;
-            if (qcnt == 0 && ccnt == 0) break;
+            uint32_t spins = 0;
+            uint64_t wait0 = tid == 0 ? global_ns() : 0;  // start of the current wait (thread 0)
+            for (;;) {
+                bool rdy = todo && ld_volatile_u32(&a.IR[slot]) == tag;
+                if (tid == 0) {
+                    sm.tcount = 0;
+                    sm.lq_tail = 0;
+                    sm.lq_work = 0;
+                }
+                __syncthreads();
+                if (rdy) {
+                    __threadfence();  // the piece was written before its tag
+                    const uint32_t pos = atomicAdd(&sm.tcount, 1u);
+                    sm.tv[pos] = a.IV[slot];
+                    sm.tb[pos] = a.IB[slot];
+                    sm.tl[pos] = a.IL[slot];
+                    todo = false;
+                }
+                __syncthreads();
+                const uint32_t got = sm.tcount;
+                if (got) {
+                    scan_block_rows<TB>(a.adj, sm.tv, sm.tb, sm.tl, got, sm.btile, visit);
+                    flush();
+                    local_loop();
+                    __syncthreads();
+                    // drained, and whatever they queued is counted: give them back
+                    if (tid == 0) {
+                        atomicAdd(&P->pending, 0ull - (unsigned long long)got);
+                        wait0 = global_ns();
+                    }
+                    spins = 0;
+                }
+                if (!__syncthreads_or(todo)) break;  // all taken slots done: take the next ones
+                if (!got) {
+                    // nothing ready: the rest may never be filled
+                    if (tid == 0) {
+                        sm.flag = 0;
+                        if (ld_volatile_u64((const uint64_t*)&P->pending) == 0) sm.flag = 1;
+                        if ((++spins & 63u) == 0 && global_ns() - wait0 > a.limit_ns) {
+                            atomicOr(&ctl->err, ERR_TIMEOUT);
+                            sm.flag = 1;
+                        }
+                        if (!sm.flag) __nanosleep(64);
+                    }
+                    __syncthreads();
+                    if (sm.flag) break;
+                }
+            }
         }
+        // ---- block totals, then the level's barrier
+        dmn = warp_min(dmn);
+        claimed = warp_sum(claimed);
+        natom = warp_sum(natom);
+        npieces = warp_sum(npieces);
+        if (lane == 0) {
+            if (dmn != 0xffffffffu) atomicMin(&sm.acc_min, dmn);
+            if (claimed) atomicAdd(&sm.acc_claimed, (unsigned long long)claimed);
+            if (natom) atomicAdd(&sm.acc_atomics, (unsigned long long)natom);
+            if (npieces) atomicAdd(&sm.acc_pieces, (unsigned long long)npieces);
+        }
+        __syncthreads();
+        const uint64_t my_n_next = sm.kept;  // read before the barrier: thread 0 clears it next level
+        if (tid == 0) {
+            if (sm.acc_min != 0xffffffffu) atomicMin(&P->nmin, sm.acc_min);
+            if (sm.acc_claimed) atomicAdd(&P->claimed, sm.acc_claimed);
+            if (sm.acc_atomics) atomicAdd(&ctl->atomics, sm.acc_atomics);
+            if (sm.acc_pieces) atomicAdd(&ctl->pieces, sm.acc_pieces);
+            atomicAdd(&ctl->rem_written, (unsigned long long)my_n_next);
+        }
+        if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+        stamp(2, k);
+        visited += ld_relaxed_u64(&P->claimed);
+        const uint32_t level_min = ld_relaxed_u32(&P->nmin);
         ++level;
         if (visited >= n) break;
         if (level_min == 0xffffffffu || level_min <= k) {
@@ -453,7 +538,6 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
     if (blockIdx.x == 0 && tid == 0) {
         ctl->stamps = nstamp;
         ctl->levels = level;
-        ctl->subrounds = subrounds;
     }
 }
 
@@ -469,23 +553,19 @@ static cudaError_t launch_kcore(CoreArgs& a, uint32_t grid, cudaStream_t s) {
     return cudaLaunchCooperativeKernel((const void*)kcore_kernel<TB>, dim3(grid), dim3(TB), params, 0, s);
 }
 
-
 dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
                      uint64_t* trace_dev, uint64_t trace_cap, uint64_t* stamps) {
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
     if (n == 0) return DSG_OK;
     const Tuning tu = tuning_for(g, 1);
-    const uint64_t chunk_cap = (uint64_t)n + (2 * g->m) / tu.chunk_len + 1;
     Scratch sc(s);
     CoreArgs a;
     a.n = n;
     a.off = g->off;
     a.adj = g->adj;
     a.limit_ns = wait_limit_ns();
-    a.short_max = tu.short_max;
     a.chunk_len = tu.chunk_len;
-    a.chunk_cap = chunk_cap;
     a.hot_deg = tu.hot_deg;
     a.local_max = tu.local_max;
     a.local_work = tu.local_work;
@@ -503,6 +583,9 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     // a block scans at most ceil(n / (grid * block)) tiles of `block` vertices
     const uint64_t span = (uint64_t)grid * tu.block;
     a.seg = ((uint64_t)n + span - 1) / span * tu.block;
+    // a level queues at most one piece per chunk_len entries of each row plus
+    // one per vertex; blocks may take slots past that and skip them
+    a.cap = (uint64_t)n + (2 * g->m) / tu.chunk_len + 1;
     bool direct = is_device_ptr(core_out);
     if (direct) a.deg = core_out;
     else DSG_TRY_CUDA(sc.get(&a.deg, n));
@@ -512,16 +595,20 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     DSG_TRY_CUDA(sc.get(&a.QA, a.seg * grid));
     DSG_TRY_CUDA(sc.get(&a.QB, a.seg * grid));
     DSG_TRY_CUDA(sc.get(&a.QL, a.seg * grid));
-    DSG_TRY_CUDA(sc.get(&a.Q, n));
-    DSG_TRY_CUDA(sc.get(&a.QgB, n));
-    DSG_TRY_CUDA(sc.get(&a.QgL, n));
-    DSG_TRY_CUDA(sc.get(&a.C, chunk_cap));
+    DSG_TRY_CUDA(sc.get(&a.IV, a.cap));
+    DSG_TRY_CUDA(sc.get(&a.IB, a.cap));
+    DSG_TRY_CUDA(sc.get(&a.IL, a.cap));
+    DSG_TRY_CUDA(sc.get(&a.IR, a.cap));
+    DSG_TRY_CUDA(cudaMemsetAsync(a.IR, 0, a.cap * sizeof(uint32_t), s));
     DSG_TRY_CUDA(sc.get(&a.ctl, 1));
     {
         CoreCtl init;
         memset(&init, 0, sizeof(init));
         init.init_min = 0xffffffffu;
-        for (int i = 0; i < 3; ++i) init.slot[i].nmin = 0xffffffffu;
+        for (int i = 0; i < 3; ++i) {
+            init.lvl[i].pending = grid;
+            init.lvl[i].nmin = 0xffffffffu;
+        }
         DSG_TRY_CUDA(cudaMemcpyAsync(a.ctl, &init, sizeof(CoreCtl), cudaMemcpyHostToDevice, s));
     }
     switch (tu.block) {
@@ -540,7 +627,8 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
         return DSG_ECUDA;
     }
     if (stamps) *stamps = c.stamps;
-    const uint64_t vals[5] = {c.levels, c.subrounds, c.rem_scanned, c.rem_written, c.atomics};
+    // levels, queued pieces, remaining vertices scanned / written, degree atomics
+    const uint64_t vals[5] = {c.levels, c.pieces, c.rem_scanned, c.rem_written, c.atomics};
     for (uint32_t i = 0; stats && i < nstats && i < 5; ++i) stats[i] = vals[i];
     return status_from_err(c.err, "kcore");
 }
