@@ -57,7 +57,9 @@ struct __align__(128) CoreLevel {
     unsigned long long pad2[15];
     unsigned long long claimed;  // vertices claimed at this level
     uint32_t nmin;               // least degree above k seen
-    uint32_t pad3[29];
+    uint32_t pad3[1];
+    unsigned long long t_own, t_queue;  // traced runs: latest %globaltimer at which a block ended each phase
+    uint32_t pad4[24];
 };
 
 struct __align__(128) CoreCtl {
@@ -206,7 +208,9 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
     const uint32_t lane = tid & 31u;
     const uint32_t n = a.n;
     uint64_t nstamp = 0;
-    // trace entries: 2 words each, (time, kind << 32 | k); kind 0 start, 1 init, 2 level
+    // trace entries: 2 words each, (time, kind << 32 | k); kind 0 start, 1 init, 2 level end;
+    // block 0's own phases: 3 scan done, 4 own rows drained, 5 queue done;
+    // after each level: 6 latest own-phase end over all blocks, 7 latest queue-phase end
     auto stamp = [&](uint32_t kind, uint32_t kk) {
         if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 1 < a.trace_cap) {
             a.trace[2 * nstamp] = global_ns();
@@ -254,6 +258,8 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             R->tail = 0;
             R->claimed = 0;
             R->nmin = 0xffffffffu;
+            R->t_own = 0;
+            R->t_queue = 0;
         }
         uint32_t dmn = 0xffffffffu;
         uint64_t claimed = 0, natom = 0, npieces = 0;
@@ -413,6 +419,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             if (lane == 0 && scanned) atomicAdd(&ctl->rem_scanned, (unsigned long long)scanned);
         }
         __syncthreads();
+        stamp(3, k);
         // ---- drain what this block's scan claimed, and what that leads to locally
         {
             const uint32_t own = (uint32_t)min((uint64_t)sm.own, a.seg);
@@ -422,6 +429,8 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         }
         // the block adds nothing more except from queue pieces: give back its token
         __syncthreads();
+        stamp(4, k);
+        if (a.trace && tid == 0) atomicMax(&P->t_own, (unsigned long long)global_ns());
         if (tid == 0) atomicAdd(&P->pending, ~0ull);  // minus one
         // ---- take queue pieces until the level has none left and no block can add any.
         // Slot s belongs to block s mod grid, so consecutive pieces go to
@@ -499,6 +508,8 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                 }
             }
         }
+        stamp(5, k);
+        if (a.trace && tid == 0) atomicMax(&P->t_queue, (unsigned long long)global_ns());
         // ---- block totals, then the level's barrier
         dmn = warp_min(dmn);
         claimed = warp_sum(claimed);
@@ -521,6 +532,14 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         }
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
         stamp(2, k);
+        if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 3 < a.trace_cap) {
+            // the grid's latest ends of the own-work and queue phases
+            a.trace[2 * nstamp] = ld_relaxed_u64(&P->t_own);
+            a.trace[2 * nstamp + 1] = (6ull << 32) | k;
+            a.trace[2 * nstamp + 2] = ld_relaxed_u64(&P->t_queue);
+            a.trace[2 * nstamp + 3] = (7ull << 32) | k;
+        }
+        if (a.trace) nstamp += 2;
         visited += ld_relaxed_u64(&P->claimed);
         const uint32_t level_min = ld_relaxed_u32(&P->nmin);
         ++level;
