@@ -91,6 +91,18 @@ dsg_status dsg_graph_csr(const dsg_graph* g, uint64_t* off, uint32_t* adj);
 /* Re-target the graph's calls to another stream. */
 dsg_status dsg_graph_set_stream(dsg_graph* g, void* stream);
 
+/* A second handle over g's device CSR, bound to `stream` (no copy; the view
+ * must be freed before g).  With views on different streams, independent
+ * solves of one graph (peels at several eps, core numbers) can be issued
+ * side by side.  No counterpart in the paper. */
+dsg_status dsg_graph_view(const dsg_graph* g, void* stream, dsg_graph** out);
+
+/* Cap the grid of the persistent kernels (peel, core numbers) launched for
+ * this handle at max_blocks blocks (0: as many as the GPU holds), so that
+ * solves on two handles, capped to fit the GPU together, run side by side;
+ * a solve's result never depends on the cap.  No counterpart in the paper. */
+dsg_status dsg_graph_set_max_blocks(dsg_graph* g, uint32_t max_blocks);
+
 /* Release a graph and its device memory.  NULL is ignored. */
 void dsg_graph_free(dsg_graph* g);
 
@@ -392,6 +404,23 @@ dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[8])
 typedef void* (*dsg_alloc_fn)(size_t bytes, void* ctx, void* stream);
 typedef void (*dsg_free_fn)(void* ptr, void* ctx, void* stream);
 void dsg_set_allocator(dsg_alloc_fn alloc, dsg_free_fn free_fn, void* ctx);
+
+/*
+ * Several Bahmani peels (eps_num[i] / eps_den[i], i < count) and the core
+ * numbers of one graph in one call: the same results as count dsg_bahmani
+ * calls plus one dsg_kcore call (out_sets[i], out_E[i], out_V[i]; out_core),
+ * with the peels and the core decomposition running side by side on two
+ * internal streams, each on half of the SMs -- unless the autotuned times of
+ * the graph's size class show the core numbers taking over four times as
+ * long as the peels, in which case they run one after the other on the whole
+ * GPU.  Results never depend on the choice.  out_sets (and its entries),
+ * out_E, out_V nullable; out_core NULL runs the peels only.  Work starts
+ * after what is queued on the graph's stream, which waits for all of it
+ * before the call returns.  No counterpart in the paper (its two algorithms
+ * are separate programs).
+ */
+dsg_status dsg_solve(const dsg_graph* g, uint32_t count, const uint32_t* eps_num, const uint32_t* eps_den,
+                     uint8_t* const* out_sets, uint64_t* out_E, uint64_t* out_V, uint32_t* out_core);
 
 /* Upper bound (ns) on every device-side wait (grid barriers, queue polls).
  * A wait that runs out makes its kernel return and the call report

@@ -264,6 +264,43 @@ class Graph:
         """CBDS-P (Algorithm 2): densest core plus the second phase's legit vertices."""
         return self._cbds(lib().dsg_cbds, "cbds", core, out_core, out_set, want_set, want_core)
 
+    def solve(self, eps, out_sets=None, out_core=None, want_sets: bool = True, want_core: bool = True):
+        """dsg_solve: Bahmani peels at every (p, q) in eps plus the core numbers,
+        side by side on the GPU.  Returns ([(mask, E, V), ...], core)."""
+        k = len(eps)
+        pn = (ctypes.c_uint32 * max(k, 1))(*[p for p, _ in eps])
+        qn = (ctypes.c_uint32 * max(k, 1))(*[q for _, q in eps])
+        if want_sets and out_sets is None:
+            out_sets = [np.empty(max(self.n, 1), np.uint8) for _ in range(k)]
+        sets = (ctypes.c_void_p * max(k, 1))(*([N.ptr(x) for x in out_sets] if want_sets else [None] * k))
+        if want_core and out_core is None:
+            out_core = np.empty(max(self.n, 1), np.uint32)
+        E = np.zeros(max(k, 1), np.uint64)
+        V = np.zeros(max(k, 1), np.uint64)
+        N.check(lib().dsg_solve(self._h, k, pn, qn, sets, E.ctypes.data_as(N._U64P), V.ctypes.data_as(N._U64P),
+                                N.ptr(out_core) if want_core else None), "solve")
+        res = []
+        for i in range(k):
+            m = out_sets[i] if want_sets else None
+            if isinstance(m, np.ndarray):
+                m = m[:self.n]
+            res.append((m, int(E[i]), int(V[i])))
+        if isinstance(out_core, np.ndarray):
+            out_core = out_core[:self.n]
+        return res, (out_core if want_core else None)
+
+    def view(self, stream=None) -> "Graph":
+        """A second handle over this graph's device CSR on `stream` (close it
+        before this graph)."""
+        h = ctypes.c_void_p()
+        N.check(lib().dsg_graph_view(self._h, N.stream_handle(stream), ctypes.byref(h)), "graph_view")
+        return Graph(h, keepalive=(self,))
+
+    def set_max_blocks(self, max_blocks: int):
+        """Cap the grid of this handle's persistent kernels (0: whole GPU), so
+        solves on two handles can share the GPU from two streams."""
+        N.check(lib().dsg_graph_set_max_blocks(self._h, int(max_blocks)), "set_max_blocks")
+
     def tuning(self, kernel: str = "peel") -> dict:
         """Launch parameters a solve of `kernel` ("peel" or "kcore") on this graph uses now."""
         v = (ctypes.c_uint32 * 8)()

@@ -115,6 +115,9 @@ _SIGS = [
     ("dsg_tune_clear", None, []),
     ("dsg_tune_entries", c.c_uint32, []),
     ("dsg_tune_lookup", c.c_int, [_VP, c.c_uint32, _U32P]),
+    ("dsg_graph_set_max_blocks", c.c_int, [_VP, c.c_uint32]),
+    ("dsg_graph_view", c.c_int, [_VP, _VP, c.POINTER(_VP)]),
+    ("dsg_solve", c.c_int, [_VP, c.c_uint32, _U32P, _U32P, c.POINTER(_VP), _U64P, _U64P, _VP]),
     ("dsg_set_inline_max", c.c_int, [c.c_uint32]),
     ("dsg_set_allocator", None, [ALLOC_FN, FREE_FN, _VP]),
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),

@@ -214,6 +214,25 @@ dsg_status dsg_graph_set_stream(dsg_graph* g, void* stream) {
     return DSG_OK;
 }
 
+dsg_status dsg_graph_view(const dsg_graph* g, void* stream, dsg_graph** out) {
+    clear_error();
+    DSG_CHECK_ARG(g && out, "graph or out is NULL");
+    dsg_graph* v = new dsg_graph(*g);
+    v->owns = false;
+    v->stream = (cudaStream_t)stream;
+    v->max_blocks = 0;
+    v->force_block = 0;
+    *out = v;
+    return DSG_OK;
+}
+
+dsg_status dsg_graph_set_max_blocks(dsg_graph* g, uint32_t max_blocks) {
+    clear_error();
+    DSG_CHECK_ARG(g, "graph is NULL");
+    g->max_blocks = max_blocks;
+    return DSG_OK;
+}
+
 dsg_status dsg_graph_csr(const dsg_graph* g, uint64_t* off, uint32_t* adj) {
     clear_error();
     DSG_CHECK_ARG(g, "graph is NULL");

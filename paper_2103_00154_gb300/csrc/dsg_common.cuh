@@ -100,6 +100,8 @@ struct dsg_graph {
     bool owns = true;        // library allocated off/adj
     int device = 0;
     cudaStream_t stream = nullptr;
+    uint32_t max_blocks = 0; // cap on the grid of persistent kernels for this handle (0: whole GPU)
+    uint32_t force_block = 0; // block size of those kernels regardless of tuning (0: tuned)
 };
 
 // -------------------------------------------------------------- device side

@@ -42,6 +42,10 @@ Tuning current_tuning();
 // autotuned entry of g's size class if there is one, else current_tuning().
 Tuning tuning_for(const dsg_graph* g, int kernel);
 
+// Autotuned solve times (ms) of g's size class for the peel (at the tuning
+// eps) and the core numbers; false unless both were tuned.
+bool tuned_times(const dsg_graph* g, double* peel_ms, double* core_ms);
+
 // Counts one kernel launch and, when profiling is on, brackets it with CUDA
 // events on its stream.  Construct right before the launch, destroy right
 // after it:  { LaunchScope ls("name", s); kernel<<<...>>>(...); }
@@ -75,10 +79,11 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
 dsg_status validate_csr(const dsg_graph* g);
 
 // Grid size for a cooperative launch of `kernel` with `block` threads and
-// `smem` dynamic shared memory, capped so small problems use few blocks.
+// `smem` dynamic shared memory, capped so small problems use few blocks (and
+// at max_grid when that is non-zero).
 template <class K>
 cudaError_t coop_grid(K kernel, uint32_t block, size_t smem, uint64_t work_items, uint32_t blocks_per_sm,
-                      uint32_t* grid) {
+                      uint32_t* grid, uint32_t max_grid = 0) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (int)block, smem);
     if (e != cudaSuccess) return e;
@@ -88,6 +93,7 @@ cudaError_t coop_grid(K kernel, uint32_t block, size_t smem, uint64_t work_items
     uint64_t need = (work_items + block - 1) / block;
     if (need < 1) need = 1;
     if (g > need) g = need;
+    if (max_grid && g > max_grid) g = max_grid;
     *grid = (uint32_t)g;
     return cudaSuccess;
 }

@@ -139,6 +139,7 @@ constexpr uint32_t kSamplePairs = 32768;    // pairs sampled to find them
 constexpr uint32_t kSampleSlots = 4096;
 constexpr uint32_t kHotMinHits = 4;         // sample hits that make a vertex hot
 constexpr uint32_t kHotEmpty = 0xffffffffu;
+constexpr uint64_t kHotPassMinPairs = 1ull << 22;  // inputs with fewer pairs skip the pass
 
 __device__ __forceinline__ uint32_t hot_hash(uint32_t x) { return (x * 0x9E3779B1u) >> 21; }  // 11 bits
 
@@ -713,18 +714,24 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     DSG_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IngestCtl), s));
     // count and scatter run on the same grid, so each block meets the same pairs
     const uint32_t pair_grid = (uint32_t)std::min<uint64_t>((m_raw + 255) / 256 + 1, (uint64_t)dev_info().sms * 8);
+    // small inputs skip the hot-endpoint pass: no address is hit often enough
+    // to matter, and its fixed cost would dominate
+    const bool hot_pass = m_raw >= kHotPassMinPairs;
     uint32_t *hot_ids, *hot_n, *blk;
     DSG_TRY_CUDA(sc.get(&hot_ids, kHotMax));
     DSG_TRY_CUDA(sc.get(&hot_n, 1));
-    DSG_TRY_CUDA(sc.get(&blk, (size_t)pair_grid * kHotMax));
-    if (m_raw) {
+    DSG_TRY_CUDA(sc.get(&blk, hot_pass ? (size_t)pair_grid * kHotMax : 1));
+    if (hot_pass) {
         { LaunchScope ls_("ingest_hot_sample", s); hot_sample<<<1, 1024, 0, s>>>(n, m_raw, src, dst, hot_ids, hot_n); }
     } else {
         DSG_TRY_CUDA(cudaMemsetAsync(hot_n, 0, 4, s));
     }
     { LaunchScope ls_("ingest_count_kernel", s); count_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, cnt, hot_ids, hot_n, blk, ctl); }
     DSG_TRY_CUDA(cudaGetLastError());
-    { LaunchScope ls_("ingest_hot_bases", s); hot_block_bases<<<kHotMax, 256, 0, s>>>(hot_n, pair_grid, blk); }
+    if (hot_pass) {
+        LaunchScope ls_("ingest_hot_bases", s);
+        hot_block_bases<<<kHotMax, 256, 0, s>>>(hot_n, pair_grid, blk);
+    }
     DSG_TRY_CUDA(cudaGetLastError());
     DSG_TRY_CUDA(device_scan(cnt, n, start, sums, s));
     { LaunchScope ls_("ingest_classify_count", s); classify_count<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, ctl); }

@@ -561,8 +561,8 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
 }
 
 template <int TB>
-static cudaError_t kcore_grid(const CoreArgs& a, uint32_t blocks_per_sm, uint32_t* grid) {
-    return coop_grid(kcore_kernel<TB>, TB, 0, a.n, blocks_per_sm, grid);
+static cudaError_t kcore_grid(const CoreArgs& a, uint32_t blocks_per_sm, uint32_t* grid, uint32_t max_grid) {
+    return coop_grid(kcore_kernel<TB>, TB, 0, a.n, blocks_per_sm, grid, max_grid);
 }
 
 template <int TB>
@@ -577,7 +577,8 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
     if (n == 0) return DSG_OK;
-    const Tuning tu = tuning_for(g, 1);
+    Tuning tu = tuning_for(g, 1);
+    if (g->force_block) tu.block = g->force_block;
     Scratch sc(s);
     CoreArgs a;
     a.n = n;
@@ -594,9 +595,9 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     uint32_t grid = 1;
     cudaError_t e;
     switch (tu.block) {
-        case 256: e = kcore_grid<256>(a, tu.blocks_per_sm, &grid); break;
-        case 1024: e = kcore_grid<1024>(a, tu.blocks_per_sm, &grid); break;
-        default: e = kcore_grid<512>(a, tu.blocks_per_sm, &grid); break;
+        case 256: e = kcore_grid<256>(a, tu.blocks_per_sm, &grid, g->max_blocks); break;
+        case 1024: e = kcore_grid<1024>(a, tu.blocks_per_sm, &grid, g->max_blocks); break;
+        default: e = kcore_grid<512>(a, tu.blocks_per_sm, &grid, g->max_blocks); break;
     }
     DSG_TRY_CUDA(e);
     // a block scans at most ceil(n / (grid * block)) tiles of `block` vertices

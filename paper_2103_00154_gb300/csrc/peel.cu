@@ -18,6 +18,9 @@
 //
 // Vertex state is one 32-bit word: an alive vertex holds its degree inside
 // S_r (< 2^31); a failed one holds 0x80000000 | (round it failed, 1-based).
+#include <string>
+#include <thread>
+
 #include "dsg_common.cuh"
 #include "dsg_kernels.cuh"
 
@@ -254,9 +257,9 @@ __global__ void peel_finish_kernel(uint32_t n, const uint32_t* __restrict__ st, 
 }
 
 template <int TB>
-static cudaError_t launch_peel(PeelArgs& a, uint32_t blocks_per_sm, cudaStream_t s) {
+static cudaError_t launch_peel(PeelArgs& a, uint32_t blocks_per_sm, cudaStream_t s, uint32_t max_grid) {
     uint32_t grid = 1;
-    cudaError_t e = coop_grid(peel_kernel<TB>, TB, 0, a.n, blocks_per_sm, &grid);
+    cudaError_t e = coop_grid(peel_kernel<TB>, TB, 0, a.n, blocks_per_sm, &grid, max_grid);
     if (e != cudaSuccess) return e;
     void* params[] = {&a};
     LaunchScope ls("peel_rounds", s);
@@ -285,7 +288,8 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
                            uint64_t* trace_dev, uint64_t trace_cap) {
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
-    const Tuning tu = tuning_for(g, 0);
+    Tuning tu = tuning_for(g, 0);
+    if (g->force_block) tu.block = g->force_block;
     memset(ctl_host, 0, sizeof(PeelCtl));
     if (n == 0) {
         static const uint64_t zero = 0;
@@ -322,9 +326,9 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
     DSG_TRY_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
     cudaError_t e;
     switch (tu.block) {
-        case 256: e = launch_peel<256>(a, tu.blocks_per_sm, s); break;
-        case 1024: e = launch_peel<1024>(a, tu.blocks_per_sm, s); break;
-        default: e = launch_peel<512>(a, tu.blocks_per_sm, s); break;
+        case 256: e = launch_peel<256>(a, tu.blocks_per_sm, s, g->max_blocks); break;
+        case 1024: e = launch_peel<1024>(a, tu.blocks_per_sm, s, g->max_blocks); break;
+        default: e = launch_peel<512>(a, tu.blocks_per_sm, s, g->max_blocks); break;
     }
     DSG_TRY_CUDA(e);
     uint32_t* pr_dev = nullptr;
@@ -381,6 +385,92 @@ dsg_status dsg_bahmani(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, u
     if (st != DSG_OK) return st;
     if (out_E) *out_E = g->n ? c.best_E : 0;
     if (out_V) *out_V = g->n ? c.best_V : 0;
+    return DSG_OK;
+}
+
+// Peels at several eps and the core numbers of one graph.  The two kinds of
+// solve are independent, so they may run side by side: the peels on one
+// internal stream and the core numbers on another (from a second host thread,
+// since each solve waits for its stream), each kernel with 1024-thread blocks
+// on at most half the SMs -- one block per SM, so the two grids fit the GPU
+// together.  Both streams start after the graph's stream, and the graph's
+// stream waits for both before the call returns.
+dsg_status dsg_solve(const dsg_graph* g, uint32_t count, const uint32_t* eps_num, const uint32_t* eps_den,
+                     uint8_t* const* out_sets, uint64_t* out_E, uint64_t* out_V, uint32_t* out_core) {
+    clear_error();
+    DSG_CHECK_ARG(g, "graph is NULL");
+    DSG_CHECK_ARG(count == 0 || (eps_num && eps_den), "eps arrays are NULL");
+    for (uint32_t i = 0; i < count; ++i) DSG_CHECK_ARG(eps_den[i] != 0, "eps_den must be positive");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    auto peels = [&](const dsg_graph* h) -> dsg_status {
+        for (uint32_t i = 0; i < count; ++i) {
+            PeelCtl c;
+            dsg_status st =
+                run_peel(h, eps_num[i], eps_den[i], nullptr, nullptr, 0, nullptr, out_sets ? out_sets[i] : nullptr, &c);
+            if (st != DSG_OK) return st;
+            if (out_E) out_E[i] = g->n ? c.best_E : 0;
+            if (out_V) out_V[i] = g->n ? c.best_V : 0;
+        }
+        return DSG_OK;
+    };
+    // side by side only pays when the peels are a fair share of the work:
+    // each kind then runs on half the GPU; when the autotuned times of this
+    // graph's size class say the core numbers dominate, run one after the
+    // other with the whole GPU each
+    double peel_ms = 0, core_ms = 0;
+    const bool mostly_core = tuned_times(g, &peel_ms, &core_ms) && count * peel_ms < 0.25 * core_ms;
+    if (count == 0 || !out_core || g->n == 0 || mostly_core) {
+        dsg_status st = peels(g);
+        if (st != DSG_OK || !out_core) return st;
+        return run_kcore(g, out_core, nullptr, 0);
+    }
+    const uint32_t sms = (uint32_t)dev_info().sms;
+    // two streams and three events per calling thread and device, made once
+    struct SideBySide {
+        int device = -1;
+        cudaStream_t sa = nullptr, sb = nullptr;
+        cudaEvent_t ev0 = nullptr, eva = nullptr, evb = nullptr;
+    };
+    static thread_local SideBySide cache[16];
+    SideBySide& sbs = cache[g->device & 15];
+    if (sbs.device != g->device) {
+        DSG_TRY_CUDA(cudaStreamCreateWithFlags(&sbs.sa, cudaStreamNonBlocking));
+        DSG_TRY_CUDA(cudaStreamCreateWithFlags(&sbs.sb, cudaStreamNonBlocking));
+        DSG_TRY_CUDA(cudaEventCreateWithFlags(&sbs.ev0, cudaEventDisableTiming));
+        DSG_TRY_CUDA(cudaEventCreateWithFlags(&sbs.eva, cudaEventDisableTiming));
+        DSG_TRY_CUDA(cudaEventCreateWithFlags(&sbs.evb, cudaEventDisableTiming));
+        sbs.device = g->device;
+    }
+    cudaStream_t sa = sbs.sa, sb = sbs.sb;
+    cudaEvent_t ev0 = sbs.ev0, eva = sbs.eva, evb = sbs.evb;
+    DSG_TRY_CUDA(cudaEventRecord(ev0, g->stream));
+    DSG_TRY_CUDA(cudaStreamWaitEvent(sa, ev0, 0));
+    DSG_TRY_CUDA(cudaStreamWaitEvent(sb, ev0, 0));
+    dsg_graph va = *g, vb = *g;
+    va.owns = vb.owns = false;
+    va.stream = sa;
+    vb.stream = sb;
+    va.force_block = vb.force_block = 1024;
+    va.max_blocks = sms / 2 > 0 ? sms / 2 : 1;
+    vb.max_blocks = sms - va.max_blocks > 0 ? sms - va.max_blocks : 1;
+    dsg_status st_core = DSG_OK;
+    std::string err_core;
+    std::thread th([&] {
+        cudaSetDevice(g->device);
+        st_core = run_kcore(&vb, out_core, nullptr, 0);
+        if (st_core != DSG_OK) err_core = dsg_last_error();
+    });
+    dsg_status st = peels(&va);
+    th.join();
+    cudaEventRecord(eva, sa);
+    cudaEventRecord(evb, sb);
+    cudaStreamWaitEvent(g->stream, eva, 0);
+    cudaStreamWaitEvent(g->stream, evb, 0);
+    if (st != DSG_OK) return st;
+    if (st_core != DSG_OK) {
+        set_error("%s", err_core.c_str());
+        return st_core;
+    }
     return DSG_OK;
 }
 

@@ -29,14 +29,30 @@ struct ProfTotal {
 };
 static std::vector<ProfTotal> g_totals;
 
+// Timing events are reused (created once, returned to the pool when their
+// times have been read), so a timed launch costs two event records and no
+// event creation.
+static std::vector<cudaEvent_t> g_event_pool;
+
+static bool take_event(cudaEvent_t* e) {  // caller holds g_prof_mu
+    if (!g_event_pool.empty()) {
+        *e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return true;
+    }
+    return cudaEventCreate(e) == cudaSuccess;
+}
+
 LaunchScope::LaunchScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
-    std::lock_guard<std::mutex> lk(g_prof_mu);
-    ++g_launches;
-    if (g_prof_on) {
-        if (cudaEventCreate((cudaEvent_t*)&a_) == cudaSuccess && cudaEventCreate((cudaEvent_t*)&b_) == cudaSuccess) {
-            cudaEventRecord((cudaEvent_t)a_, s_);
-            timed_ = true;
-        }
+    bool take = false;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        ++g_launches;
+        take = g_prof_on && take_event((cudaEvent_t*)&a_) && take_event((cudaEvent_t*)&b_);
+    }
+    if (take) {
+        cudaEventRecord((cudaEvent_t)a_, s_);
+        timed_ = true;
     }
 }
 
@@ -52,8 +68,8 @@ static void drain_pending() {
         float ms = 0;
         cudaEventSynchronize(e.b);
         cudaEventElapsedTime(&ms, e.a, e.b);
-        cudaEventDestroy(e.a);
-        cudaEventDestroy(e.b);
+        g_event_pool.push_back(e.a);
+        g_event_pool.push_back(e.b);
         ProfTotal* t = nullptr;
         for (auto& x : g_totals)
             if (x.name == e.name) t = &x;

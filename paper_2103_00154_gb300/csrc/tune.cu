@@ -200,6 +200,17 @@ Tuning tuning_for(const dsg_graph* g, int kernel) {
     return it == g_table.end() ? base : it->second;
 }
 
+// Autotuned solve times (ms) of g's size class, when both kernels were tuned.
+bool tuned_times(const dsg_graph* g, double* peel_ms, double* core_ms) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto a = g_table_ms.find(class_key(g, 0));
+    auto b = g_table_ms.find(class_key(g, 1));
+    if (a == g_table_ms.end() || b == g_table_ms.end()) return false;
+    *peel_ms = a->second;
+    *core_ms = b->second;
+    return true;
+}
+
 dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
                      uint64_t* trace_dev, uint64_t trace_cap, uint64_t* stamps);
 dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4]);
