@@ -84,9 +84,12 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cbds", action="store_true", help="skip the densest-core / CBDS-P timing")
-    ap.add_argument("--solve", action="store_true",
-                    help="run each step's peels and core numbers with one dsg_solve call (side by side on the GPU) "
-                         "instead of one dsg_bahmani call per eps and one dsg_kcore call")
+    ap.add_argument("--step-api", choices=["separate", "solve"], default="separate",
+                    help="device-timed steps: one dsg_bahmani call per eps and one dsg_kcore call (default; "
+                         "each kernel bracketed by its own timing events), or one dsg_solve call")
+    ap.add_argument("--e2e-api", choices=["separate", "solve"], default="solve",
+                    help="end-to-end steps (host buffers, no per-kernel events): dsg_solve (default) or "
+                         "separate calls")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-parameter autotuner before warm-up")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in the batch workload")
@@ -298,7 +301,7 @@ def run_ours(args, wl, raw, rank, world):
 
     def step():
         g = dsg.Graph.from_edges(n, src_d, dst_d, stream=stream)
-        if not args.solve:
+        if args.step_api == "separate":
             for i, (p, q) in enumerate(wl["eps"]):
                 _, E, V = g.bahmani(p, q, out_set=masks[i])
                 results[(p, q)] = (E, V)
@@ -430,7 +433,7 @@ def run_e2e(args, wl, raw, dev, edges_per_step, world):
 
     def step():
         g = dsg.Graph.from_edges(n, src_h, dst_h, stream=stream)
-        if not args.solve:
+        if args.e2e_api == "separate":
             for i, (p, q) in enumerate(wl["eps"]):
                 g.bahmani(p, q, out_set=masks[i])
             g.kcore(out=core_h)
@@ -797,10 +800,15 @@ def main():
                        "m": res["m"], "edges_scanned_per_step": res["edges_per_step"],
                        "l2": "flushed before every timed step (512 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "step": ("dsg_graph_from_edges, then one dsg_bahmani per eps and dsg_kcore" if not args.solve else
-                                "dsg_graph_from_edges, then dsg_solve (the peels and the core numbers side by side "
-                                "on half the GPU each unless the tuned times say the core numbers dominate); "
-                                "per-kernel times are taken on each kernel's own stream"),
+                       "step": {"device_timed": "dsg_graph_from_edges, then " + (
+                                    "one dsg_bahmani per eps and dsg_kcore, each kernel bracketed by timing events"
+                                    if args.step_api == "separate" else
+                                    "dsg_solve (peels and core numbers side by side), each kernel bracketed by "
+                                    "timing events on its own stream"),
+                                "e2e": "host buffers: dsg_graph_from_edges, then " + (
+                                    "dsg_solve (peels and core numbers side by side on half the GPU each unless "
+                                    "the tuned times say the core numbers dominate)" if args.e2e_api == "solve"
+                                    else "one dsg_bahmani per eps and dsg_kcore")},
                        "tuning": res["tuning"]},
             "graphs_per_s": world * args.steps / (res["ms_per_step"] * args.steps / 1e3),
             "roofline": res["roofline"],
