@@ -433,9 +433,8 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
             fn(bu, bv, valid);
         }
     }
-    if (LOCAL) return;
-    // ---- long rows, one warp per chunk item
-    for (uint64_t it = clo + gw; it < chi; it += nw) {
+    // ---- long rows, one warp per chunk item (none for a block-private list)
+    for (uint64_t it = LOCAL ? chi : clo + gw; it < chi; it += nw) {
         uint64_t item = C[it];
         uint32_t v = (uint32_t)(item >> 32);
 #ifdef DSG_DEBUG_BOUNDS

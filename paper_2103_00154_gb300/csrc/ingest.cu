@@ -135,9 +135,9 @@ static cudaError_t device_scan(const uint32_t* in, uint64_t n, uint64_t* out, ui
 // vertices are hot only changes speed, never the result.
 constexpr uint32_t kHotMax = 1024;          // hot vertices at most
 constexpr uint32_t kHotSlots = 2048;        // shared-memory hash of the hot ids
-constexpr uint32_t kSamplePairs = 32768;    // pairs sampled to find them
-constexpr uint32_t kSampleSlots = 4096;
-constexpr uint32_t kHotMinHits = 4;         // sample hits that make a vertex hot
+constexpr uint32_t kSamplePairs = 8192;     // pairs sampled to find them
+constexpr uint32_t kSampleSlots = 8192;     // room for every distinct endpoint of most samples
+constexpr uint32_t kHotMinHits = 2;         // sample hits that make a vertex hot
 constexpr uint32_t kHotEmpty = 0xffffffffu;
 constexpr uint64_t kHotPassMinPairs = 1ull << 22;  // inputs with fewer pairs skip the pass
 
@@ -147,8 +147,9 @@ __device__ __forceinline__ uint32_t hot_hash(uint32_t x) { return (x * 0x9E3779B
 __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
                                                    const uint32_t* __restrict__ dst, uint32_t* __restrict__ hot_ids,
                                                    uint32_t* __restrict__ hot_n) {
-    __shared__ uint32_t key[kSampleSlots];
-    __shared__ uint32_t cnt[kSampleSlots];
+    extern __shared__ uint32_t sample_smem[];  // kSampleSlots keys, then kSampleSlots counts
+    uint32_t* key = sample_smem;
+    uint32_t* cnt = sample_smem + kSampleSlots;
     __shared__ uint32_t nsel;
     for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x) {
         key[i] = kHotEmpty;
@@ -174,9 +175,10 @@ __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, c
         for (uint32_t t = 0; t < 2 * kU; ++t) {
             const uint32_t x = e[t];
             if (x >= n || e[t ^ 1u] == x) continue;  // out of range, padding or a loop
-            uint32_t h = (x * 0x9E3779B1u) >> 20;  // 12 bits
+            uint32_t h = (x * 0x9E3779B1u) >> 19;  // 13 bits
             for (uint32_t probe = 0; probe < 8; ++probe, h = (h + 1) & (kSampleSlots - 1)) {
-                const uint32_t prev = atomicCAS(&key[h], kHotEmpty, x);
+                const uint32_t cur = key[h];
+                const uint32_t prev = cur == x ? x : (cur == kHotEmpty ? atomicCAS(&key[h], kHotEmpty, x) : cur);
                 if (prev == kHotEmpty || prev == x) {
                     atomicAdd(&cnt[h], 1u);
                     break;
@@ -722,7 +724,13 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     DSG_TRY_CUDA(sc.get(&hot_n, 1));
     DSG_TRY_CUDA(sc.get(&blk, hot_pass ? (size_t)pair_grid * kHotMax : 1));
     if (hot_pass) {
-        { LaunchScope ls_("ingest_hot_sample", s); hot_sample<<<1, 1024, 0, s>>>(n, m_raw, src, dst, hot_ids, hot_n); }
+        const size_t smem = 2 * kSampleSlots * sizeof(uint32_t);
+        static bool smem_set[64] = {};  // the attribute is per function and device, set once (idempotent)
+        if (!smem_set[dev & 63]) {
+            DSG_TRY_CUDA(cudaFuncSetAttribute(hot_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            smem_set[dev & 63] = true;
+        }
+        { LaunchScope ls_("ingest_hot_sample", s); hot_sample<<<1, 1024, smem, s>>>(n, m_raw, src, dst, hot_ids, hot_n); }
     } else {
         DSG_TRY_CUDA(cudaMemsetAsync(hot_n, 0, 4, s));
     }

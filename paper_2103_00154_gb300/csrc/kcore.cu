@@ -59,7 +59,8 @@ struct __align__(128) CoreLevel {
     uint32_t nmin;               // least degree above k seen
     uint32_t pad3[1];
     unsigned long long t_own, t_queue;  // traced runs: latest %globaltimer at which a block ended each phase
-    uint32_t pad4[24];
+    unsigned long long scan_claims, pieces;  // traced runs: claims by the scan, row pieces queued
+    uint32_t pad4[20];
 };
 
 struct __align__(128) CoreCtl {
@@ -210,7 +211,8 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
     uint64_t nstamp = 0;
     // trace entries: 2 words each, (time, kind << 32 | k); kind 0 start, 1 init, 2 level end;
     // block 0's own phases: 3 scan done, 4 own rows drained, 5 queue done;
-    // after each level: 6 latest own-phase end over all blocks, 7 latest queue-phase end
+    // after each level: 6 latest own-phase end over all blocks, 7 latest queue-phase end,
+    // then (value, kind) pairs 8 claims, 9 claims by the scan, 10 queued pieces
     auto stamp = [&](uint32_t kind, uint32_t kk) {
         if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 1 < a.trace_cap) {
             a.trace[2 * nstamp] = global_ns();
@@ -260,16 +262,20 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             R->nmin = 0xffffffffu;
             R->t_own = 0;
             R->t_queue = 0;
+            R->scan_claims = 0;
+            R->pieces = 0;
         }
         uint32_t dmn = 0xffffffffu;
-        uint64_t claimed = 0, natom = 0, npieces = 0;
+        uint64_t claimed = 0, natom = 0, npieces = 0, nscan_claims = 0;
         // u reached k: drain it in this block if there is room, else queue it
         // (a scan still running elsewhere may have taken it first)
         auto reach_k = [&](uint32_t u) {
+            // the row bounds are loaded alongside the claim (one round trip)
+            const uint64_t beg = a.off[u];
+            const uint64_t end = a.off[u + 1];
             if (!claim_vertex(a.claim, u)) return;
             ++claimed;
-            const uint64_t beg = a.off[u];
-            const uint64_t len = a.off[u + 1] - beg;
+            const uint64_t len = end - beg;
             if (len <= a.local_max && atomicAdd(&sm.lq_work, (uint32_t)len) + len <= a.local_work) {
                 uint32_t pos = atomicAdd(&sm.lq_tail, 1u);
                 if (pos < CoreSmem<TB>::kLocalQ) {
@@ -366,52 +372,84 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             sm.acc_pieces = 0;
         }
         __syncthreads();
-        // ---- scan: claim degree <= k, keep degree > k, drop the claimed
+        // ---- scan: claim degree <= k, keep degree > k, drop the claimed.
+        // kScanU tiles per step, their loads issued together.
         {
+            constexpr uint32_t kScanU = TB >= 1024 ? 2 : 4;  // 1024-thread blocks have 64 registers
             uint32_t mn = 0xffffffffu;
             const uint64_t lim = my_rem ? my_n : n;
             const uint64_t stride = my_rem ? TB : (uint64_t)gridDim.x * TB;
             uint64_t scanned = 0;
-            for (uint64_t t = my_rem ? 0 : (uint64_t)blockIdx.x * TB; t < lim; t += stride) {
-                const uint64_t i = t + tid;
-                bool keep = false;
-                uint32_t v = 0;
-                if (i < lim) {
+            for (uint64_t t = my_rem ? 0 : (uint64_t)blockIdx.x * TB; t < lim; t += kScanU * stride) {
+                uint32_t v[kScanU], dv[kScanU], cw[kScanU];
+                bool in[kScanU];
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u) {
+                    const uint64_t i = t + u * stride + tid;
+                    in[u] = i < lim;
+                    v[u] = in[u] ? (my_rem ? my_rem[i] : (uint32_t)i) : 0u;
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u) {
+                    dv[u] = in[u] ? deg[v[u]] : 0u;
+                    cw[u] = in[u] ? a.claim[v[u] >> 5] : 0u;
+                }
+                bool keep[kScanU], mine[kScanU];
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u) {
+                    keep[u] = false;
+                    mine[u] = false;
+                    if (!in[u]) continue;
                     ++scanned;
-                    v = my_rem ? my_rem[i] : (uint32_t)i;
-                    const uint32_t dv = deg[v];
-                    const uint32_t taken = a.claim[v >> 5] >> (v & 31u) & 1u;
-                    if (!taken) {
-                        if (dv > k) {
-                            keep = true;
-                            mn = min(mn, dv);
-                        } else if (claim_vertex(a.claim, v)) {
-                            ++claimed;
-                            const uint64_t beg = a.off[v];
-                            const uint64_t len = a.off[v + 1] - beg;
-                            // drained by this block, or, for rows above inline_max,
-                            // queued in pieces for every block
-                            if (len <= a.inline_max) {
-                                uint32_t pos = atomicAdd(&sm.own, 1u);
-                                DSG_BOUND(ctl, 5, pos, a.seg, level, pos = 0);
-                                myQA[pos] = v;
-                                myQB[pos] = beg;
-                                myQL[pos] = (uint32_t)len;
-                            } else {
-                                npieces += queue_row(a, P, tag, v, beg, len);
-                            }
-                        }
+                    if (cw[u] >> (v[u] & 31u) & 1u) continue;  // taken earlier
+                    if (dv[u] > k) {
+                        keep[u] = true;
+                        mn = min(mn, dv[u]);
+                    } else {
+                        mine[u] = true;  // a candidate: claimed below
                     }
                 }
-                // keep: warp ballot, one shared-memory atomic per warp
-                const uint32_t bal = __ballot_sync(kFullMask, keep);
-                uint32_t base = 0;
-                if (lane == 0 && bal) base = atomicAdd(&sm.kept, (uint32_t)__popc(bal));
-                base = __shfl_sync(kFullMask, base, 0);
-                if (keep) {
-                    uint64_t at = base + __popc(bal & lanemask_lt());
-                    DSG_BOUND(ctl, 3, at, a.seg, level, keep = false);
-                    if (keep) my_rem_next[at] = v;
+                // row bounds of the candidates, loaded alongside their claims
+                uint64_t beg[kScanU], len[kScanU];
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u) {
+                    beg[u] = mine[u] ? a.off[v[u]] : 0;
+                    len[u] = mine[u] ? a.off[v[u] + 1] : 0;
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u)
+                    if (mine[u]) mine[u] = claim_vertex(a.claim, v[u]);
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u) {
+                    if (!mine[u]) continue;
+                    ++claimed;
+                    ++nscan_claims;
+                    const uint64_t ln = len[u] - beg[u];
+                    // drained by this block, or, for rows above inline_max,
+                    // queued in pieces for every block
+                    if (ln <= a.inline_max) {
+                        uint32_t pos = atomicAdd(&sm.own, 1u);
+                        DSG_BOUND(ctl, 5, pos, a.seg, level, pos = 0);
+                        myQA[pos] = v[u];
+                        myQB[pos] = beg[u];
+                        myQL[pos] = (uint32_t)ln;
+                    } else {
+                        npieces += queue_row(a, P, tag, v[u], beg[u], ln);
+                    }
+                }
+                // keep: warp ballot, one shared-memory atomic per warp and tile
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u) {
+                    const uint32_t bal = __ballot_sync(kFullMask, keep[u]);
+                    uint32_t base = 0;
+                    if (lane == 0 && bal) base = atomicAdd(&sm.kept, (uint32_t)__popc(bal));
+                    base = __shfl_sync(kFullMask, base, 0);
+                    if (keep[u]) {
+                        uint64_t at = base + __popc(bal & lanemask_lt());
+                        bool ok = true;
+                        DSG_BOUND(ctl, 3, at, a.seg, level, ok = false);
+                        if (ok) my_rem_next[at] = v[u];
+                    }
                 }
             }
             dmn = min(dmn, mn);
@@ -509,7 +547,12 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             }
         }
         stamp(5, k);
-        if (a.trace && tid == 0) atomicMax(&P->t_queue, (unsigned long long)global_ns());
+        if (a.trace) {
+            const uint64_t sc = warp_sum(nscan_claims), pc = warp_sum(npieces);
+            if (lane == 0 && sc) atomicAdd(&P->scan_claims, (unsigned long long)sc);
+            if (lane == 0 && pc) atomicAdd(&P->pieces, (unsigned long long)pc);
+            if (tid == 0) atomicMax(&P->t_queue, (unsigned long long)global_ns());
+        }
         // ---- block totals, then the level's barrier
         dmn = warp_min(dmn);
         claimed = warp_sum(claimed);
@@ -532,14 +575,21 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         }
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
         stamp(2, k);
-        if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 3 < a.trace_cap) {
-            // the grid's latest ends of the own-work and queue phases
+        if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 9 < a.trace_cap) {
+            // the grid's latest ends of the own-work and queue phases, and the
+            // level's claims (all / by the scan) and queued pieces
             a.trace[2 * nstamp] = ld_relaxed_u64(&P->t_own);
             a.trace[2 * nstamp + 1] = (6ull << 32) | k;
             a.trace[2 * nstamp + 2] = ld_relaxed_u64(&P->t_queue);
             a.trace[2 * nstamp + 3] = (7ull << 32) | k;
+            a.trace[2 * nstamp + 4] = ld_relaxed_u64(&P->claimed);
+            a.trace[2 * nstamp + 5] = (8ull << 32) | k;
+            a.trace[2 * nstamp + 6] = ld_relaxed_u64(&P->scan_claims);
+            a.trace[2 * nstamp + 7] = (9ull << 32) | k;
+            a.trace[2 * nstamp + 8] = ld_relaxed_u64(&P->pieces);
+            a.trace[2 * nstamp + 9] = (10ull << 32) | k;
         }
-        if (a.trace) nstamp += 2;
+        if (a.trace) nstamp += 5;
         visited += ld_relaxed_u64(&P->claimed);
         const uint32_t level_min = ld_relaxed_u32(&P->nmin);
         ++level;
