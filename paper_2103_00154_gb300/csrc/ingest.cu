@@ -135,9 +135,9 @@ static cudaError_t device_scan(const uint32_t* in, uint64_t n, uint64_t* out, ui
 // vertices are hot only changes speed, never the result.
 constexpr uint32_t kHotMax = 1024;          // hot vertices at most
 constexpr uint32_t kHotSlots = 2048;        // shared-memory hash of the hot ids
-constexpr uint32_t kSamplePairs = 8192;     // pairs sampled to find them
-constexpr uint32_t kSampleSlots = 8192;     // room for every distinct endpoint of most samples
-constexpr uint32_t kHotMinHits = 2;         // sample hits that make a vertex hot
+constexpr uint32_t kSamplePairs = 32768;    // pairs sampled to find them
+constexpr uint32_t kSampleSlots = 8192;     // shared-memory hash of the sampled endpoints
+constexpr uint32_t kHotMinHits = 4;         // sample hits that make a vertex hot
 constexpr uint32_t kHotEmpty = 0xffffffffu;
 constexpr uint64_t kHotPassMinPairs = 1ull << 22;  // inputs with fewer pairs skip the pass
 
@@ -187,8 +187,29 @@ __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, c
         }
     }
     __syncthreads();
+    // keep the most frequent: a histogram of the hit counts (capped at 255)
+    // gives the count above which all fit, and the boundary count fills the rest
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t cut, room, extra;
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x)
+        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) atomicAdd(&hist[min(cnt[i], 255u)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0, b = 255;
+        while (b >= kHotMinHits && acc + hist[b] <= kHotMax) acc += hist[b--];
+        cut = b;                // buckets above cut are taken whole
+        room = kHotMax - acc;  // slots left for bucket cut
+        extra = 0;
+    }
+    __syncthreads();
     for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x) {
-        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) {
+        if (key[i] == kHotEmpty || cnt[i] < kHotMinHits) continue;
+        const uint32_t bk = min(cnt[i], 255u);
+        bool take = bk > cut;
+        if (!take && bk == cut) take = atomicAdd(&extra, 1u) < room;
+        if (take) {
             const uint32_t at = atomicAdd(&nsel, 1u);
             if (at < kHotMax) hot_ids[at] = key[i];
         }
