@@ -143,10 +143,28 @@ constexpr uint64_t kHotPassMinPairs = 1ull << 22;  // inputs with fewer pairs sk
 
 __device__ __forceinline__ uint32_t hot_hash(uint32_t x) { return (x * 0x9E3779B1u) >> 21; }  // 11 bits
 
-// One block: count endpoint frequencies over a strided sample of the pairs.
-__global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
-                                                   const uint32_t* __restrict__ dst, uint32_t* __restrict__ hot_ids,
-                                                   uint32_t* __restrict__ hot_n) {
+__host__ __device__ __forceinline__ uint64_t sample_stride(uint64_t m_raw) {
+    return m_raw > kSamplePairs ? m_raw / kSamplePairs : 1;
+}
+__host__ __device__ __forceinline__ uint64_t sample_take(uint64_t m_raw) {
+    return m_raw < kSamplePairs ? m_raw : kSamplePairs;
+}
+
+// Gather every stride-th pair into one contiguous buffer, a pair per thread
+// over many SMs (one block fetching 32 K scattered pairs is bound by its own
+// outstanding loads).
+__global__ void __launch_bounds__(256) hot_gather(uint64_t m_raw, const uint32_t* __restrict__ src,
+                                                  const uint32_t* __restrict__ dst, uint2* __restrict__ sample) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < sample_take(m_raw)) {
+        const uint64_t at = k * sample_stride(m_raw);
+        sample[k] = make_uint2(src[at], dst[at]);
+    }
+}
+
+// One block: count endpoint frequencies over the gathered sample.
+__global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, const uint2* __restrict__ sample,
+                                                   uint32_t* __restrict__ hot_ids, uint32_t* __restrict__ hot_n) {
     extern __shared__ uint32_t sample_smem[];  // kSampleSlots keys, then kSampleSlots counts
     uint32_t* key = sample_smem;
     uint32_t* cnt = sample_smem + kSampleSlots;
@@ -157,8 +175,7 @@ __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, c
     }
     if (threadIdx.x == 0) nsel = 0;
     __syncthreads();
-    const uint64_t stride = m_raw > kSamplePairs ? m_raw / kSamplePairs : 1;
-    const uint64_t take = m_raw < kSamplePairs ? m_raw : kSamplePairs;
+    const uint64_t take = sample_take(m_raw);
     constexpr uint32_t kU = 8;  // pairs loaded per thread before any is counted
     for (uint64_t k0 = threadIdx.x; k0 < take; k0 += (uint64_t)blockDim.x * kU) {
         uint32_t e[2 * kU];
@@ -167,8 +184,9 @@ __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, c
             const uint64_t k = k0 + (uint64_t)t * blockDim.x;
             e[2 * t] = e[2 * t + 1] = kHotEmpty;
             if (k < take) {
-                e[2 * t] = src[k * stride];
-                e[2 * t + 1] = dst[k * stride];
+                const uint2 p = sample[k];
+                e[2 * t] = p.x;
+                e[2 * t + 1] = p.y;
             }
         }
 #pragma unroll
@@ -751,7 +769,13 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
             DSG_TRY_CUDA(cudaFuncSetAttribute(hot_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             smem_set[dev & 63] = true;
         }
-        { LaunchScope ls_("ingest_hot_sample", s); hot_sample<<<1, 1024, smem, s>>>(n, m_raw, src, dst, hot_ids, hot_n); }
+        uint2* sample;
+        DSG_TRY_CUDA(sc.get(&sample, (size_t)sample_take(m_raw)));
+        {
+            LaunchScope ls_("ingest_hot_gather", s);
+            hot_gather<<<(uint32_t)((sample_take(m_raw) + 255) / 256), 256, 0, s>>>(m_raw, src, dst, sample);
+        }
+        { LaunchScope ls_("ingest_hot_sample", s); hot_sample<<<1, 1024, smem, s>>>(n, m_raw, sample, hot_ids, hot_n); }
     } else {
         DSG_TRY_CUDA(cudaMemsetAsync(hot_n, 0, 4, s));
     }

@@ -1,5 +1,6 @@
 // Core numbers by the level-synchronous peel of Algorithm 2's first phase
-// (PKC), as one persistent cooperative kernel with one grid barrier per level.
+// (PKC), as one persistent cooperative kernel; the blocks meet once per level,
+// on a counter of outstanding work rather than a separate grid barrier.
 //
 // Level k (Alg. 2 first phase):
 //   scan: every block walks its own segment of the remaining vertices; degree
@@ -14,12 +15,15 @@
 //     PKC's thread-local buffer); everything else goes to a level-wide queue
 //     of row pieces (at most chunk_len entries each) that blocks with no
 //     work of their own take from as it comes, so neither hub rows nor
-//     cascades that outgrow one block cost an extra grid barrier;
+//     cascades that outgrow one block cost an extra grid-wide wait;
 //   the level ends when the queue is drained and no block can add to it: a
 //     counter holds one token per block (given back when its scan and own
 //     draining are done) plus one per queued piece (given back once the piece
 //     and everything it led the block to do locally are done), and the level
-//     is over when it reaches zero;
+//     is over when it reaches zero.  Each block adds its least degree above
+//     k and its claims to the level's totals before every give-back, so the
+//     totals are final once the counter is zero and each block goes on to
+//     the next level as soon as it sees that, with no grid barrier;
 //   "visited" grows by the frontier size (Alg. 2 "atomicAdd(visited, end)").
 // Scan and drain overlap, so a vertex is taken into the frontier by claiming
 // its bit in a bitmap (atomicOr): whichever of the scan and the decrement that
@@ -33,10 +37,11 @@
 // When visited == n, deg[v] is the core number of v.
 //
 // Per-level counters (queue tail, the token count, claims, least
-// degree) sit in a ring of three sets, level L using set L % 3: blocks read a
-// level's claims and least degree right after its barrier, so block 0 re-arms
-// set (L+1) % 3 at the start of level L -- two barriers after that set's
-// last reads, one barrier before its next use.  Queue slots are reused by
+// degree) sit in a ring of three sets, level L using set L % 3.  Block 0
+// re-arms set (L+1) % 3 at the start of level L, before it gives back its
+// level-L token: no block uses that set before it has seen level L's count at
+// zero, and every block read the set's last totals (level L-2's) before it
+// gave back its level-(L-1) token, which block 0 waited for.  Queue slots are reused by
 // every level; a slot is published by writing the level's tag (level + 1)
 // after its contents, so a stale slot is never taken for a new one.
 #include <string.h>
@@ -132,7 +137,11 @@ struct CoreArgs {
 template <int TB>
 constexpr uint32_t local_q_cap() { return TB >= 1024 ? 640 : 1024; }
 
-constexpr uint32_t kTakeSlots = 8;  // queue slots a block takes at a time
+#ifndef DSG_TAKE_SLOTS
+#define DSG_TAKE_SLOTS 32
+#endif
+constexpr uint32_t kTakeSlots = DSG_TAKE_SLOTS;  // queue slots a block takes at a time
+static_assert(kTakeSlots >= 1 && kTakeSlots <= 32, "a block takes 1..32 queue slots at a time");
 
 template <int TB>
 struct CoreSmem {
@@ -152,8 +161,10 @@ struct CoreSmem {
     uint32_t tl[kTakeSlots];  // ... entries
     uint32_t tcount;
     uint32_t flag;
-    uint32_t acc_min;       // block reductions at the end of a level
-    unsigned long long acc_claimed, acc_atomics, acc_pieces;
+    uint32_t acc_min;       // block reductions: least degree above k, claims (published during the level) ...
+    unsigned long long acc_claimed, acc_atomics, acc_pieces;  // ... and statistics (end of the level)
+    unsigned long long lvl_claimed;  // the level's totals, read once it is over
+    uint32_t lvl_min, lvl_err;
     uint32_t redm[33];
 };
 
@@ -192,7 +203,7 @@ __device__ __forceinline__ uint64_t queue_row(const CoreArgs& a, CoreLevel* P, u
         a.IB[at] = beg + c * a.chunk_len;
         a.IL[at] = (uint32_t)min((uint64_t)a.chunk_len, len - c * a.chunk_len);
     }
-    __threadfence();
+    // each tag is a release store: the lane's piece is visible before its tag
     for (uint64_t c = 0; c < np; ++c) {
         const uint64_t at = s0 + c;
         DSG_BOUND(a.ctl, 6, at, a.cap, tag, break);
@@ -361,6 +372,27 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                 lq_lo = lq_hi;
             }
         };
+        // Publish the least degree above k and the claims this block has seen
+        // since it last did, before the token or pieces that cover them are
+        // given back: whoever sees the level's count reach zero then reads
+        // final totals, with no grid barrier.
+        auto publish = [&]() {
+            const uint32_t wm = warp_min(dmn);
+            const uint64_t wc = warp_sum(claimed);
+            if (lane == 0) {
+                if (wm != 0xffffffffu) atomicMin(&sm.acc_min, wm);
+                if (wc) atomicAdd(&sm.acc_claimed, (unsigned long long)wc);
+            }
+            dmn = 0xffffffffu;
+            claimed = 0;
+            __syncthreads();
+            if (tid == 0) {
+                if (sm.acc_min != 0xffffffffu) atomicMin(&P->nmin, sm.acc_min);
+                if (sm.acc_claimed) atomicAdd(&P->claimed, sm.acc_claimed);
+                sm.acc_min = 0xffffffffu;
+                sm.acc_claimed = 0;
+            }
+        };
         if (tid == 0) {
             sm.lq_tail = 0;
             sm.lq_work = 0;
@@ -466,20 +498,18 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             local_loop();
         }
         // the block adds nothing more except from queue pieces: give back its token
-        __syncthreads();
+        publish();
         stamp(4, k);
         if (a.trace && tid == 0) atomicMax(&P->t_own, (unsigned long long)global_ns());
-        if (tid == 0) atomicAdd(&P->pending, ~0ull);  // minus one
+        if (tid == 0) {
+            __threadfence();  // the block's work and totals before its token
+            atomicAdd(&P->pending, ~0ull);  // minus one
+        }
         // ---- take queue pieces until the level has none left and no block can add any.
         // Slot s belongs to block s mod grid, so consecutive pieces go to
         // different blocks; a block takes its next kTakeSlots slots at a time.
+        // Each poll loads the slots' tags and the level's count together.
         for (uint64_t round = 0;; round += kTakeSlots) {
-            if (tid == 0) {
-                sm.flag = 0;
-                if (ld_volatile_u64((const uint64_t*)&P->pending) == 0 || (ld_volatile_u32(&ctl->err) & ERR_TIMEOUT)) sm.flag = 1;
-            }
-            __syncthreads();
-            if (sm.flag) break;
             const uint64_t slot = (uint64_t)blockIdx.x + (round + tid) * gridDim.x;
             bool todo = tid < kTakeSlots && slot < a.cap;
             if (!__syncthreads_or(todo)) {
@@ -499,16 +529,20 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             }
             uint32_t spins = 0;
             uint64_t wait0 = tid == 0 ? global_ns() : 0;  // start of the current wait (thread 0)
+            bool over = false;
             for (;;) {
-                bool rdy = todo && ld_volatile_u32(&a.IR[slot]) == tag;
+                const bool rdy = todo && ld_acquire_u32(&a.IR[slot]) == tag;  // the piece was written before its tag
                 if (tid == 0) {
                     sm.tcount = 0;
                     sm.lq_tail = 0;
                     sm.lq_work = 0;
+                    // zero with this block's slots unready: a ready slot holds a
+                    // piece the count still covers
+                    sm.flag = ld_volatile_u64((const uint64_t*)&P->pending) == 0 ||
+                              (ld_volatile_u32(&ctl->err) & ERR_TIMEOUT);
                 }
                 __syncthreads();
                 if (rdy) {
-                    __threadfence();  // the piece was written before its tag
                     const uint32_t pos = atomicAdd(&sm.tcount, 1u);
                     sm.tv[pos] = a.IV[slot];
                     sm.tb[pos] = a.IB[slot];
@@ -521,30 +555,22 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                     scan_block_rows<TB>(a.adj, sm.tv, sm.tb, sm.tl, got, sm.btile, visit);
                     flush();
                     local_loop();
-                    __syncthreads();
-                    // drained, and whatever they queued is counted: give them back
+                    // drained, and whatever they queued is counted: publish, then give them back
+                    publish();
                     if (tid == 0) {
+                        __threadfence();
                         atomicAdd(&P->pending, 0ull - (unsigned long long)got);
                         wait0 = global_ns();
                     }
                     spins = 0;
+                } else if (sm.flag) {
+                    over = true;  // the level is over
                 }
-                if (!__syncthreads_or(todo)) break;  // all taken slots done: take the next ones
-                if (!got) {
-                    // nothing ready: the rest may never be filled
-                    if (tid == 0) {
-                        sm.flag = 0;
-                        if (ld_volatile_u64((const uint64_t*)&P->pending) == 0) sm.flag = 1;
-                        if ((++spins & 63u) == 0 && global_ns() - wait0 > a.limit_ns) {
-                            atomicOr(&ctl->err, ERR_TIMEOUT);
-                            sm.flag = 1;
-                        }
-                        if (!sm.flag) __nanosleep(64);
-                    }
-                    __syncthreads();
-                    if (sm.flag) break;
-                }
+                if (over || !__syncthreads_or(todo)) break;  // over, or all taken slots done: take the next ones
+                if (!got && tid == 0 && (++spins & 63u) == 0 && global_ns() - wait0 > a.limit_ns)
+                    atomicOr(&ctl->err, ERR_TIMEOUT);  // seen at the next poll
             }
+            if (over) break;
         }
         stamp(5, k);
         if (a.trace) {
@@ -553,36 +579,41 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             if (lane == 0 && pc) atomicAdd(&P->pieces, (unsigned long long)pc);
             if (tid == 0) atomicMax(&P->t_queue, (unsigned long long)global_ns());
         }
-        // ---- block totals, then the level's barrier
-        dmn = warp_min(dmn);
-        claimed = warp_sum(claimed);
+        // ---- the level is over: its totals are final (published before every
+        // give-back); statistics are summed for the host
         natom = warp_sum(natom);
         npieces = warp_sum(npieces);
         if (lane == 0) {
-            if (dmn != 0xffffffffu) atomicMin(&sm.acc_min, dmn);
-            if (claimed) atomicAdd(&sm.acc_claimed, (unsigned long long)claimed);
             if (natom) atomicAdd(&sm.acc_atomics, (unsigned long long)natom);
             if (npieces) atomicAdd(&sm.acc_pieces, (unsigned long long)npieces);
         }
-        __syncthreads();
-        const uint64_t my_n_next = sm.kept;  // read before the barrier: thread 0 clears it next level
         if (tid == 0) {
-            if (sm.acc_min != 0xffffffffu) atomicMin(&P->nmin, sm.acc_min);
-            if (sm.acc_claimed) atomicAdd(&P->claimed, sm.acc_claimed);
+            __threadfence();  // the count was seen at zero: every block's totals are visible
+            sm.lvl_claimed = ld_volatile_u64((const uint64_t*)&P->claimed);
+            sm.lvl_min = ld_volatile_u32(&P->nmin);
+            sm.lvl_err = ld_volatile_u32(&ctl->err) & ERR_TIMEOUT;
+        }
+        __syncthreads();
+        const uint64_t my_n_next = sm.kept;
+        const uint64_t lvl_claimed = sm.lvl_claimed;
+        const uint32_t level_min = sm.lvl_min;
+        if (sm.lvl_err) return;
+        if (tid == 0) {
             if (sm.acc_atomics) atomicAdd(&ctl->atomics, sm.acc_atomics);
             if (sm.acc_pieces) atomicAdd(&ctl->pieces, sm.acc_pieces);
             atomicAdd(&ctl->rem_written, (unsigned long long)my_n_next);
         }
-        if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
+        __syncthreads();  // every thread has read the block's totals before they are reset
         stamp(2, k);
         if (a.trace && blockIdx.x == 0 && tid == 0 && 2 * nstamp + 9 < a.trace_cap) {
-            // the grid's latest ends of the own-work and queue phases, and the
-            // level's claims (all / by the scan) and queued pieces
+            // the latest ends of the own-work and queue phases over the blocks
+            // (as block 0 sees them: the queue phase of some blocks may still be
+            // ending), and the level's claims (all / by the scan) and queued pieces
             a.trace[2 * nstamp] = ld_relaxed_u64(&P->t_own);
             a.trace[2 * nstamp + 1] = (6ull << 32) | k;
             a.trace[2 * nstamp + 2] = ld_relaxed_u64(&P->t_queue);
             a.trace[2 * nstamp + 3] = (7ull << 32) | k;
-            a.trace[2 * nstamp + 4] = ld_relaxed_u64(&P->claimed);
+            a.trace[2 * nstamp + 4] = lvl_claimed;
             a.trace[2 * nstamp + 5] = (8ull << 32) | k;
             a.trace[2 * nstamp + 6] = ld_relaxed_u64(&P->scan_claims);
             a.trace[2 * nstamp + 7] = (9ull << 32) | k;
@@ -590,8 +621,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             a.trace[2 * nstamp + 9] = (10ull << 32) | k;
         }
         if (a.trace) nstamp += 5;
-        visited += ld_relaxed_u64(&P->claimed);
-        const uint32_t level_min = ld_relaxed_u32(&P->nmin);
+        visited += lvl_claimed;
         ++level;
         if (visited >= n) break;
         if (level_min == 0xffffffffu || level_min <= k) {
