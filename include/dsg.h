@@ -188,7 +188,7 @@ dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const uint32_t* 
 dsg_status dsg_kcore(const dsg_graph* g, uint32_t* out_core);
 
 /* As dsg_kcore, also writing up to nstats counters of the run into stats:
- *   [0] levels run (one grid barrier each)
+ *   [0] levels run (the blocks meet once per level, on its work counter)
  *   [1] row pieces queued to the level-wide work queue
  *   [2] remaining-list entries scanned (sum over levels)
  *   [3] remaining-list entries written (sum over levels)
@@ -444,8 +444,13 @@ dsg_status dsg_debug_wait_timeout(uint32_t which, uint64_t limit_ns);
  *                          at kernel start and after every grid barrier
  *                          (2 per round) into ts[cap]; *count = stamps taken
  *   dsg_debug_kcore_trace  one core decomposition recording pairs
- *                          (ns, kind << 32 | k), kind 0 start, 1 init,
- *                          2 level scan, 3 drain sub-round; *count = pairs
+ *                          (ns, kind << 32 | k): kind 0 start, 1 degrees
+ *                          initialised, 2 level over (block 0), 3/4/5 block
+ *                          0's scan / own rows / queue phase done; after
+ *                          each level five (value, kind << 32 | k) pairs:
+ *                          6/7 latest own / queue phase end over the blocks
+ *                          (ns, as block 0 sees them), 8 claims, 9 claims by
+ *                          the scan, 10 queued row pieces; *count = pairs
  *   dsg_debug_barrier_ns   average latency of one grid barrier of a
  *                          co-resident grid (block threads, blocks_per_sm,
  *                          0 = occupancy limit) over iters barriers
