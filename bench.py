@@ -192,11 +192,11 @@ def kcore_bytes(n: int, m: int, st: dict) -> int:
     """Algorithmic bytes of one core-number launch: adjacency 8m; offsets of
     every frontier vertex 16n; degree init write 4n and claim-bitmap clear
     n/8; per level the remaining id, degree and claim word read 12|R_k|
-    (level 0 reads no id); one claim atomic per vertex 4n; per adjacency
-    entry one degree read 4 B; each degree atomic (decrement or undo) 4 B
-    write; remaining-list writes 4 B each."""
-    return (8 * m + 16 * n + 4 * n + n // 8 + 12 * st["rem_scanned"] - 4 * n + 4 * n + 4 * 2 * m
-            + 4 * st["atomics"] + 4 * st["rem_written"])
+    (level 0 reads no id); one claim atomic per vertex 4n; each degree atomic
+    (one decrement per adjacency entry, and the undos) reads and writes 4 B;
+    remaining-list writes 4 B each."""
+    return (8 * m + 16 * n + 4 * n + n // 8 + 12 * st["rem_scanned"] - 4 * n + 4 * n
+            + 8 * st["atomics"] + 4 * st["rem_written"])
 
 
 KERNEL_SOURCES = {

@@ -309,10 +309,11 @@ void dsg_serve_destroy(dsg_server* s);
  */
 dsg_status dsg_set_tuning(uint32_t block, uint32_t blocks_per_sm, uint32_t short_max, uint32_t chunk_len);
 dsg_status dsg_get_tuning(uint32_t* block, uint32_t* blocks_per_sm, uint32_t* short_max, uint32_t* chunk_len);
-/* Degree at or above which decrements of a vertex are first combined in a
- * per-block shared-memory table (one global atomic per block and phase for a
- * hub instead of one per edge).  0 (the default) means four times the number
- * of blocks of the launch; DSG_HOT_DEG.  Results never depend on it. */
+/* Bahmani peel: degree at or above which decrements of a vertex are first
+ * combined in a per-block shared-memory table (one global atomic per block and
+ * phase for a hub instead of one per edge).  0 (the default) means four times
+ * the number of blocks of the launch; DSG_HOT_DEG.  Results never depend on
+ * it.  The core numbers decrement every neighbour at once and ignore it. */
 dsg_status dsg_set_hot_degree(uint32_t hot_deg);
 /* Core numbers: a vertex whose row has at most local_max entries and that
  * reaches the current level while a block drains is drained by that block

@@ -272,8 +272,10 @@ __device__ __forceinline__ void scan_block_rows(const uint32_t* __restrict__ adj
 // pre(j) is issued for every position of a step before the owners are
 // searched (so its loads overlap the search), and a lane finds each
 // position's row among the next 32 row starts (one coalesced read by the
-// warp) with a 5-step shuffle search, or -- past a run of empty rows -- by a
-// binary search over the row starts above them.
+// warp) with a 5-step shuffle search; positions past those 32 rows (runs of
+// short or empty rows) find their 32-row block from a coarse sample of the
+// row starts (one coalesced read over 1,024 rows) and their row by a 5-step
+// binary search inside it.
 // fn(owner[], j[], pre[], valid) is called by all lanes together, bit t of
 // valid set when slot t holds a position.
 constexpr uint32_t kWalkU = 4;
@@ -330,17 +332,60 @@ __device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ of
                     done |= 1u << t;
                 }
             }
-            // past a run of empty rows: binary search above the window
-            // (off[base + 32] <= j < off[n])
+            // positions past the window (runs of short or empty rows): every
+            // pending position lies at or above off[b].  Lane l reads
+            // off[b + S l] (one coalesced read; S rows apart), a position's
+            // count of those <= it names the S-row block holding its row, and
+            // a binary search over that block's row starts (log2 S steps, all
+            // lanes and slots at once) places it.  Positions beyond the 32
+            // blocks move b up by 31 S; a pass that places nothing widens S;
+            // after 64 passes a plain binary search places what is left.
+            uint64_t b = (uint64_t)base + 32, S = 32;
+            for (uint32_t pass = 0; __any_sync(kFullMask, done != (1u << kWalkU) - 1); ++pass) {
+                if (pass == 64) {
+                    // rows spread very far apart: a binary search over [b, n) places the rest
 #pragma unroll
-            for (uint32_t t = 0; t < kWalkU; ++t) {
-                if (done >> t & 1u) continue;
-                uint32_t a = base + 32, z = n;
-                while (z - a > 1) {
-                    const uint32_t mid = a + ((z - a) >> 1);
-                    if (off[mid] <= j[t]) a = mid; else z = mid;
+                    for (uint32_t t = 0; t < kWalkU; ++t) {
+                        if (done >> t & 1u) continue;
+                        uint64_t lo = b, hi = n;  // off[b] <= j < off[n]
+                        while (hi - lo > 1) {
+                            const uint64_t mid = lo + ((hi - lo) >> 1);
+                            if (off[mid] <= j[t]) lo = mid; else hi = mid;
+                        }
+                        owner[t] = (uint32_t)lo;
+                        done |= 1u << t;
+                    }
+                    break;
                 }
-                owner[t] = a;
+                const uint64_t cidx = b + S * lane;
+                const uint64_t cw = off[cidx < n ? cidx : n];  // off[n] = total: above every position
+                const uint64_t cw31 = __shfl_sync(kFullMask, cw, 31);
+                uint32_t placed = 0;
+#pragma unroll
+                for (uint32_t t = 0; t < kWalkU; ++t) {
+                    uint32_t c = 0;
+#pragma unroll
+                    for (uint32_t step = 16; step > 0; step >>= 1) {
+                        const uint64_t wv = __shfl_sync(kFullMask, cw, c + step - 1);
+                        if (wv <= j[t]) c += step;
+                    }
+                    if (c == 31 && cw31 <= j[t]) c = 32;
+                    if (!(done >> t & 1u) && c < 32) {
+                        // off[b + S (c-1)] <= j < off[min(b + S c, n)]; c >= 1 since off[b] <= j
+                        uint64_t lo = b + S * (c - 1), hi = b + S * c;
+                        if (hi > n) hi = n;
+                        while (hi - lo > 1) {
+                            const uint64_t mid = lo + ((hi - lo) >> 1);
+                            if (off[mid] <= j[t]) lo = mid; else hi = mid;
+                        }
+                        owner[t] = (uint32_t)lo;
+                        done |= 1u << t;
+                        ++placed;
+                    }
+                }
+                // what is still pending lies at or above off[b + 31 S]
+                b += 31 * S;
+                if (!__any_sync(kFullMask, placed != 0)) S *= 32;
             }
         }
         fn(owner, j, pv, valid);
@@ -369,18 +414,23 @@ __device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ of
 // this block's warps walk it; C is ignored.
 // FB / FL (nullable): row starts and lengths stored beside F, saving the
 // offset loads of the short rows.
+// grab (nullable, grid-wide walks only): a counter, zero when the walk
+// starts, from which warps take the next short-row group or chunk item as
+// they finish the last (instead of every nw-th item), so no warp is left
+// with the heavy items while the others wait at the next barrier.
 template <int TB, bool LOCAL = false, class Fn>
 __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
                                               const uint32_t* F, uint64_t lo, uint64_t hi,
                                               const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
                                               uint32_t chunk_len, Fn& fn, uint32_t dbg_n = 0,
-                                              const uint64_t* FB = nullptr, const uint32_t* FL = nullptr) {
+                                              const uint64_t* FB = nullptr, const uint32_t* FL = nullptr,
+                                              unsigned long long* grab = nullptr) {
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31u;
     const uint64_t gw = LOCAL ? (uint64_t)(tid >> 5) : ((uint64_t)blockIdx.x * TB + tid) >> 5;
     const uint64_t nw = LOCAL ? (uint64_t)(TB >> 5) : ((uint64_t)gridDim.x * TB) >> 5;
     // ---- short rows, 32 per warp, edge-balanced over the warp's lanes
-    for (uint64_t g0 = lo + gw * 32; g0 < hi; g0 += nw * 32) {
+    auto short_group = [&](uint64_t g0) {
         uint64_t i = g0 + lane;
         uint32_t v = 0, len = 0;
         uint64_t b = 0;
@@ -432,16 +482,16 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
             }
             fn(bu, bv, valid);
         }
-    }
-    // ---- long rows, one warp per chunk item (none for a block-private list)
-    for (uint64_t it = LOCAL ? chi : clo + gw; it < chi; it += nw) {
+    };
+    // ---- long rows, one warp per chunk item
+    auto chunk_item = [&](uint64_t it) {
         uint64_t item = C[it];
         uint32_t v = (uint32_t)(item >> 32);
 #ifdef DSG_DEBUG_BOUNDS
         if (v >= dbg_n) {
             uint32_t bu[kBatch] = {0xfffffffdu}, bv[kBatch] = {v};
             fn(bu, bv, 1u);
-            continue;
+            return;
         }
 #endif
         uint64_t c = item & 0xffffffffull;
@@ -462,7 +512,28 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
             }
             fn(bu, bv, valid);
         }
+    };
+    if (!LOCAL && grab) {
+        const uint64_t ngroups = hi > lo ? (hi - lo + 31) / 32 : 0;
+        const uint64_t nchunks = chi - clo;
+        // dynamic: warps take the next short group or chunk item from a
+        // counter (zero at the start of the walk), the next grab issued
+        // while the current item is walked
+        const uint64_t nitems = ngroups + nchunks;
+        unsigned long long cur = 0;
+        if (lane == 0) cur = atomicAdd(grab, 1ull);
+        cur = __shfl_sync(kFullMask, cur, 0);
+        while (cur < nitems) {
+            unsigned long long nxt = 0;
+            if (lane == 0) nxt = atomicAdd(grab, 1ull);
+            if (cur < ngroups) short_group(lo + cur * 32);
+            else chunk_item(clo + (cur - ngroups));
+            cur = __shfl_sync(kFullMask, nxt, 0);
+        }
+        return;
     }
+    for (uint64_t g0 = lo + gw * 32; g0 < hi; g0 += nw * 32) short_group(g0);
+    for (uint64_t it = LOCAL ? chi : clo + gw; it < chi; it += nw) chunk_item(it);
 }
 
 }  // namespace dsg

@@ -881,8 +881,12 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     if (e == cudaSuccess) e = dev_alloc((void**)&g->adj, (size_t)(total2 ? total2 : 1) * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         if (total2) {
+            // one resident wave: every warp walks an equal share of the positions
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, copy_rows, 256, 0) != cudaSuccess || per_sm < 1)
+                per_sm = 1;
             LaunchScope ls_("ingest_copy_rows", s);
-            copy_rows<<<(uint32_t)dev_info().sms * 8, 256, 0, s>>>(n, start, tmp, g->off, g->adj);
+            copy_rows<<<(uint32_t)dev_info().sms * (uint32_t)per_sm, 256, 0, s>>>(n, start, tmp, g->off, g->adj);
         }
         e = cudaGetLastError();
     }

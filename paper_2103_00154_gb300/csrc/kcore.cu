@@ -4,12 +4,15 @@
 //
 // Level k (Alg. 2 first phase):
 //   scan: every block walks its own segment of the remaining vertices; degree
-//     <= k joins the level's frontier (Alg. 2 "if v.deg = k: buff[end++] <-
-//     v"), degree > k stays in the (compacted) segment;
-//   drain: for every frontier vertex v and neighbour u with deg[u] > k,
+//     <= k joins the level's frontier (Algorithm 2's per-thread buffer),
+//     degree > k stays in the (compacted) segment;
+//   drain: for every frontier vertex v and every neighbour u,
 //     a = atomicSub(deg[u], 1); a == k+1 puts u in the frontier (it just
-//     reached k); a <= k is undone with atomicAdd (another thread got there
-//     first) -- Alg. 2's drain loop.  A block drains the rows its scan found
+//     reached k); a <= k is undone with atomicAdd (u was already at or below
+//     k) -- Algorithm 2's drain, except that Algorithm 2 first reads deg[u]
+//     and skips u at or below k: decrementing at once saves one dependent
+//     memory round trip per link of a cascade and leaves the same degrees.
+//     A block drains the rows its scan found
 //     (up to inline_max entries each) and the vertices that reach k while it
 //     drains (rows up to local_max entries, while its local budget lasts:
 //     PKC's thread-local buffer); everything else goes to a level-wide queue
@@ -24,7 +27,7 @@
 //     k and its claims to the level's totals before every give-back, so the
 //     totals are final once the counter is zero and each block goes on to
 //     the next level as soon as it sees that, with no grid barrier;
-//   "visited" grows by the frontier size (Alg. 2 "atomicAdd(visited, end)").
+//   the count of visited vertices grows by the frontier size (as in Algorithm 2).
 // Scan and drain overlap, so a vertex is taken into the frontier by claiming
 // its bit in a bitmap (atomicOr): whichever of the scan and the decrement that
 // brought it to k claims it first drains it, exactly once.  A scanned degree
@@ -123,7 +126,6 @@ struct CoreArgs {
     CoreCtl* ctl;
     uint64_t limit_ns;
     uint32_t chunk_len;
-    uint32_t hot_deg;
     uint32_t local_max;   // rows up to this length found while draining stay in the block
     uint32_t local_work;  // ... while the block's local entries per batch stay within this
     uint32_t inline_max;  // rows up to this length claimed by a block's scan are drained by that block
@@ -148,7 +150,6 @@ struct CoreSmem {
     static constexpr uint32_t kLocalQ = local_q_cap<TB>();
     TileSmem<TB> tile;
     BlockTile<TB> btile;
-    AggTable agg;
     uint32_t lq[kLocalQ];   // vertices ...
     uint64_t lqb[kLocalQ];  // ... their row starts
     uint32_t lql[kLocalQ];  // ... and row lengths
@@ -232,8 +233,6 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         ++nstamp;
     };
     stamp(0, 0);
-    agg_clear(sm.agg);
-    const uint32_t hot = hot_threshold(a.hot_deg);
     // ---- init: deg = row length, claims cleared; least degree -> first level
     {
         uint32_t mn = 0xffffffffu;
@@ -298,67 +297,40 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             }
             if (len) npieces += queue_row(a, P, tag, u, beg, len);
         };
-        // c was just taken from u's degree, which was old: keep what brings
-        // it down to k, give back the rest (Algorithm 2's undo, for c units),
-        // and report the crossing into k
-        auto settle = [&](uint32_t u, uint32_t old, uint32_t c) {
+        // one unit was just taken from u's degree, which was old: a degree
+        // already at or below k gets it back (Algorithm 2's undo); reaching k
+        // makes u the level's to drain
+        auto settle = [&](uint32_t u, uint32_t old) {
             if (old <= k) {
-                atomicAdd(&deg[u], c);
+                atomicAdd(&deg[u], 1u);
                 ++natom;
                 return;
             }
-            uint32_t legit = min(c, old - k);
-            if (legit < c) {
-                atomicAdd(&deg[u], c - legit);
-                ++natom;
-            }
-            uint32_t nv = old - legit;
+            const uint32_t nv = old - 1;
             if (nv == k) reach_k(u);
             else dmn = min(dmn, nv);
         };
+        // every neighbour of a drained vertex loses one degree at once (no
+        // read first: one memory round trip less per link of a cascade); a
+        // neighbour already at or below k gets it back in settle
         auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
-            uint32_t d[kBatch], old[kBatch], need = 0;
+            uint32_t old[kBatch], need = 0;
 #pragma unroll
             for (uint32_t jj = 0; jj < kBatch; ++jj) {
-                if (!(valid >> jj & 1u)) continue;
+                if (!(valid >> jj & 1u) || u[jj] == v[jj]) continue;
 #ifdef DSG_DEBUG_BOUNDS
                 if (u[jj] >= n) {
                     DSG_BOUND(ctl, 4, u[jj], n, level, (void)0);
                     continue;
                 }
 #endif
-                if (u[jj] == v[jj]) continue;
-                d[jj] = deg[u[jj]];
+                old[jj] = atomicSub(&deg[u[jj]], 1u);
+                ++natom;
                 need |= 1u << jj;
             }
 #pragma unroll
-            for (uint32_t jj = 0; jj < kBatch; ++jj) {
-                if (!(need >> jj & 1u)) continue;
-                if (d[jj] <= k || (d[jj] >= hot && agg_add(sm.agg, u[jj]))) {
-                    need &= ~(1u << jj);  // already at k, or settled at the flush
-                    continue;
-                }
-                old[jj] = atomicSub(&deg[u[jj]], 1u);
-                ++natom;
-            }
-#pragma unroll
             for (uint32_t jj = 0; jj < kBatch; ++jj)
-                if (need >> jj & 1u) settle(u[jj], old[jj], 1u);
-        };
-        auto flush = [&]() {
-            __syncthreads();
-            for (uint32_t i = tid; i < kAggSlots; i += TB) {
-                uint32_t key = sm.agg.key[i];
-                if (key != kAggEmpty) {
-                    uint32_t c = sm.agg.cnt[i];
-                    sm.agg.key[i] = kAggEmpty;
-                    sm.agg.cnt[i] = 0;
-                    uint32_t old = atomicSub(&deg[key], c);
-                    ++natom;
-                    settle(key, old, c);
-                }
-            }
-            __syncthreads();
+                if (need >> jj & 1u) settle(u[jj], old[jj]);
         };
         // drain what this block found, until it finds nothing more
         auto local_loop = [&]() {
@@ -368,7 +340,6 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                 if (lq_lo >= lq_hi) break;
                 scan_block_rows<TB>(a.adj, sm.lq + lq_lo, sm.lqb + lq_lo, sm.lql + lq_lo, lq_hi - lq_lo, sm.btile,
                                     visit);
-                flush();
                 lq_lo = lq_hi;
             }
         };
@@ -494,7 +465,6 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         {
             const uint32_t own = (uint32_t)min((uint64_t)sm.own, a.seg);
             scan_block_rows<TB>(a.adj, myQA, myQB, myQL, own, sm.btile, visit);
-            flush();
             local_loop();
         }
         // the block adds nothing more except from queue pieces: give back its token
@@ -553,7 +523,6 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                 const uint32_t got = sm.tcount;
                 if (got) {
                     scan_block_rows<TB>(a.adj, sm.tv, sm.tb, sm.tl, got, sm.btile, visit);
-                    flush();
                     local_loop();
                     // drained, and whatever they queued is counted: publish, then give them back
                     publish();
@@ -666,7 +635,6 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     a.adj = g->adj;
     a.limit_ns = wait_limit_ns();
     a.chunk_len = tu.chunk_len;
-    a.hot_deg = tu.hot_deg;
     a.local_max = tu.local_max;
     a.local_work = tu.local_work;
     a.inline_max = tu.inline_max;

@@ -2,19 +2,21 @@
 // peel as one persistent cooperative kernel.
 //
 // Per round r, with S_r and E_r = |E(S_r)| known to every block:
-//   phase 1 (Alg. 1 part 1, "parallel for v in active"): every alive vertex is
+//   phase 1 (Algorithm 1's first part, over the active vertices): every alive vertex is
 //     tested against T_r = floor(2(p+q)E_r / (q|S_r|)), i.e. deg <= 2(1+eps)rho
 //     exactly; failures are marked and queued (short rows by vertex, long rows
 //     as chunk items), survivors are compacted into the next alive list
 //     (warp ballot + block scan + one atomic per block and list);
-//   grid barrier (Alg. 1 "barrier synchronization");
+//   grid barrier (Algorithm 1's synchronisation between its two parts);
 //   phase 2 (Alg. 1 part 2): every adjacency entry u of every failed v is read
 //     once; an alive u loses one degree (atomicSub) and the edge counts as
 //     removed; an edge whose both ends failed this round counts once (u > v);
-//     block-reduced removal counts go to one global counter (Alg. 1 "reduce");
+//     block-reduced removal counts go to one global counter (Algorithm 1's
+//     reduction of the removed edges);
 //   grid barrier; every block derives S_{r+1}, E_{r+1} from the monotone
 //   counters; block 0 records the history and keeps the densest set (strict
-//   ">", Alg. 1 "if rho > rho~").
+//   ">": a later round replaces the best only when strictly denser, as in
+//   Algorithm 1).
 //
 // Vertex state is one 32-bit word: an alive vertex holds its degree inside
 // S_r (< 2^31); a failed one holds 0x80000000 | (round it failed, 1-based).
@@ -45,6 +47,8 @@ struct __align__(128) PeelCtl {
     unsigned long long pad6[15];
     unsigned long long dec;     // alive-neighbour decrements
     unsigned long long pad7[15];
+    unsigned long long grab;    // next phase-2 item to take (zeroed in phase 1)
+    unsigned long long pad8[15];
     unsigned long long rounds, best_round, best_E, best_V;
     unsigned long long stamps;
 };
@@ -163,6 +167,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
             }
             __syncthreads();
         }
+        if (blockIdx.x == 0 && tid == 0) ctl->grab = 0;  // no warp takes phase-2 items until the barrier
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
         stamp();
         const uint64_t failed_hi = ld_relaxed_u64(&ctl->failed);
@@ -193,7 +198,11 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                 }
             }
         };
-        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n);
+#ifndef DSG_PEEL_DYNAMIC
+#define DSG_PEEL_DYNAMIC 0
+#endif
+        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n,
+                          nullptr, nullptr, DSG_PEEL_DYNAMIC ? &ctl->grab : nullptr);
         // flush the combined hub decrements (block_sum below synchronises first)
         __syncthreads();
         for (uint32_t i = tid; i < kAggSlots; i += TB) {

@@ -279,13 +279,12 @@ extern "C" dsg_status dsg_autotune(const dsg_graph* g, uint32_t eps_num, uint32_
                                    {&Tuning::chunk_len, {128, 256, 1024}, 3},
                                    {&Tuning::short_max, {16, 32, 64}, 3}};
         const Knob core_knobs[] = {{&Tuning::block, {256, 512, 1024}, 3},
-                                   {&Tuning::hot_deg, {0, 1024, 4096, 16384}, 4},
                                    {&Tuning::local_max, {256, 1024, 4096}, 3},
                                    {&Tuning::local_work, {4096, 16384, 65536}, 3},
                                    {&Tuning::inline_max, {256, 1024, 4096, 16384}, 4},
                                    {&Tuning::chunk_len, {256, 1024, 2048}, 3}};
         const Knob* knobs = kernel == 0 ? peel_knobs : core_knobs;
-        const int nknobs = kernel == 0 ? 4 : 6;
+        const int nknobs = kernel == 0 ? 4 : 5;
         for (int kk = 0; kk < nknobs; ++kk) {
             for (int vi = 0; vi < knobs[kk].count; ++vi) {
                 Tuning cand = best;

@@ -101,6 +101,15 @@ def test_power_law(gen):
     check_all(raw, tag=gen)
 
 
+@pytest.mark.parametrize("n,gap", [(70_000, 1_100), (1 << 20, 65_537)])
+def test_rows_spread_far_apart(n, gap):
+    # non-empty rows far apart: the histogram's edge walker crosses long runs
+    # of empty rows (coarse samples, widened samples, the pass limit)
+    ids = np.arange(0, n - 1, gap, dtype=np.int64)
+    pairs = np.concatenate([np.stack([ids, ids + 1], 1), [[1, 2], [2, 3], [1, 3]]])
+    check_all(inputs.from_pairs(n, pairs), tag=f"spread n={n} gap={gap}")
+
+
 def test_supplied_values_host_device_and_global_histogram():
     raw = inputs.er_block(n=9000, m=40000, k=60, p=0.5, seed=7)
     c = oracle.from_raw(raw)

@@ -144,6 +144,34 @@ def test_rmat_small(scale):
         check_peel(g, c, *pq, tag=f"rmat{scale}")
 
 
+def spread_rows_cases():
+    """Graphs whose non-empty rows sit far apart: the edge walker's steps cross
+    runs of empty rows of every length (one 32-row window, the 1,024-row
+    coarse sample, a widened sample, and steps whose rows are so far apart
+    that the pass limit hands them to the plain binary search)."""
+    out = []
+    for n, gap in [(70_000, 1_100), (300_000, 40_000), (5_000, 37), (1 << 20, 65_537)]:
+        ids = np.arange(0, n - 1, gap, dtype=np.int64)
+        out.append(inputs.from_pairs(n, np.stack([ids, ids + 1], 1), f"pairs_n{n}_gap{gap}"))
+    # stars with 1..60 leaves, centres 5,000 apart, leaves right after each centre
+    rng = np.random.default_rng(7)
+    pairs = []
+    for c0 in range(0, 200_000 - 64, 5_000):
+        for t in range(1, int(rng.integers(1, 61)) + 1):
+            pairs.append((c0, c0 + t))
+    out.append(inputs.from_pairs(200_000, pairs, "far_stars"))
+    return out
+
+
+@pytest.mark.parametrize("raw", spread_rows_cases(), ids=lambda r: r.name)
+def test_rows_spread_far_apart(raw):
+    c = oracle.from_raw(raw)
+    g = gpu_graph(raw)
+    check_csr(g, c, raw.name)
+    check_core(g, c, raw.name)
+    check_peel(g, c, 1, 10, raw.name)
+
+
 def test_ingest_row_classes_at_scale():
     # R-MAT scale 17 plus a Chung-Lu graph with 20k-degree hubs: rows land in
     # every sort class (warp 1/2/4/8/16/32 values per lane, block, and giant
