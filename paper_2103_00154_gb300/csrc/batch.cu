@@ -126,9 +126,10 @@ __device__ void peel_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
 }
 
 // Algorithm 2, first phase, on one graph by one block: level k collects the
-// remaining vertices of degree k, then drains them (atomicSub; a == k+1 joins
-// the level; a <= k is undone); the level's frontier is one FIFO in global
-// memory with a shared-memory cursor.
+// remaining vertices of degree k, then drains them (atomicSub on every
+// neighbour; a == k+1 joins the level; a <= k is undone, so a vertex already
+// at or below k never reads k+1 again); the level's frontier is one FIFO in
+// global memory with a shared-memory cursor.
 template <int TB>
 __device__ void kcore_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
     const uint32_t tid = threadIdx.x;
@@ -177,17 +178,16 @@ __device__ void kcore_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
         uint32_t q_lo = visited, q_hi = sm.u32[0];
         __syncthreads();
         while (q_lo < q_hi) {
+            // every neighbour loses one degree at once (no read first); one
+            // already at or below k gets it back
             auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
-                uint32_t d[kBatch], need = 0, old[kBatch];
+                uint32_t need = 0, old[kBatch];
 #pragma unroll
                 for (uint32_t j = 0; j < kBatch; ++j) {
                     if (!(valid >> j & 1u) || u[j] == v[j]) continue;
-                    d[j] = deg[u[j]];
-                    if (d[j] > k) need |= 1u << j;
+                    old[j] = atomicSub(&deg[u[j]], 1u);
+                    need |= 1u << j;
                 }
-#pragma unroll
-                for (uint32_t j = 0; j < kBatch; ++j)
-                    if (need >> j & 1u) old[j] = atomicSub(&deg[u[j]], 1u);
 #pragma unroll
                 for (uint32_t j = 0; j < kBatch; ++j) {
                     if (!(need >> j & 1u)) continue;

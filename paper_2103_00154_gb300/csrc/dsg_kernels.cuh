@@ -414,17 +414,12 @@ __device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ of
 // this block's warps walk it; C is ignored.
 // FB / FL (nullable): row starts and lengths stored beside F, saving the
 // offset loads of the short rows.
-// grab (nullable, grid-wide walks only): a counter, zero when the walk
-// starts, from which warps take the next short-row group or chunk item as
-// they finish the last (instead of every nw-th item), so no warp is left
-// with the heavy items while the others wait at the next barrier.
 template <int TB, bool LOCAL = false, class Fn>
 __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
                                               const uint32_t* F, uint64_t lo, uint64_t hi,
                                               const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
                                               uint32_t chunk_len, Fn& fn, uint32_t dbg_n = 0,
-                                              const uint64_t* FB = nullptr, const uint32_t* FL = nullptr,
-                                              unsigned long long* grab = nullptr) {
+                                              const uint64_t* FB = nullptr, const uint32_t* FL = nullptr) {
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31u;
     const uint64_t gw = LOCAL ? (uint64_t)(tid >> 5) : ((uint64_t)blockIdx.x * TB + tid) >> 5;
@@ -513,25 +508,6 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
             fn(bu, bv, valid);
         }
     };
-    if (!LOCAL && grab) {
-        const uint64_t ngroups = hi > lo ? (hi - lo + 31) / 32 : 0;
-        const uint64_t nchunks = chi - clo;
-        // dynamic: warps take the next short group or chunk item from a
-        // counter (zero at the start of the walk), the next grab issued
-        // while the current item is walked
-        const uint64_t nitems = ngroups + nchunks;
-        unsigned long long cur = 0;
-        if (lane == 0) cur = atomicAdd(grab, 1ull);
-        cur = __shfl_sync(kFullMask, cur, 0);
-        while (cur < nitems) {
-            unsigned long long nxt = 0;
-            if (lane == 0) nxt = atomicAdd(grab, 1ull);
-            if (cur < ngroups) short_group(lo + cur * 32);
-            else chunk_item(clo + (cur - ngroups));
-            cur = __shfl_sync(kFullMask, nxt, 0);
-        }
-        return;
-    }
     for (uint64_t g0 = lo + gw * 32; g0 < hi; g0 += nw * 32) short_group(g0);
     for (uint64_t it = LOCAL ? chi : clo + gw; it < chi; it += nw) chunk_item(it);
 }

@@ -47,8 +47,6 @@ struct __align__(128) PeelCtl {
     unsigned long long pad6[15];
     unsigned long long dec;     // alive-neighbour decrements
     unsigned long long pad7[15];
-    unsigned long long grab;    // next phase-2 item to take (zeroed in phase 1)
-    unsigned long long pad8[15];
     unsigned long long rounds, best_round, best_E, best_V;
     unsigned long long stamps;
 };
@@ -167,7 +165,6 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
             }
             __syncthreads();
         }
-        if (blockIdx.x == 0 && tid == 0) ctl->grab = 0;  // no warp takes phase-2 items until the barrier
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
         stamp();
         const uint64_t failed_hi = ld_relaxed_u64(&ctl->failed);
@@ -198,11 +195,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                 }
             }
         };
-#ifndef DSG_PEEL_DYNAMIC
-#define DSG_PEEL_DYNAMIC 0
-#endif
-        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n,
-                          nullptr, nullptr, DSG_PEEL_DYNAMIC ? &ctl->grab : nullptr);
+        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n);
         // flush the combined hub decrements (block_sum below synchronises first)
         __syncthreads();
         for (uint32_t i = tid; i < kAggSlots; i += TB) {
