@@ -206,21 +206,35 @@ KERNEL_SOURCES = {
 }
 
 
-def kernel_source_sha(name: str) -> str:
-    """Hash of the sources a kernel is built from (its file and the shared headers)."""
+def code_only(src: bytes) -> bytes:
+    """Source text without // comments, trailing blanks and empty lines: what
+    the compiler sees, so a comment edit does not retire a capture."""
+    import re
+    lines = (re.sub(rb"//.*$", b"", ln).rstrip() for ln in src.splitlines())
+    return b"\n".join(ln for ln in lines if ln)
+
+
+def kernel_source_sha(name: str, read=None) -> str:
+    """Hash of the code a kernel is built from (its file and the shared
+    headers, comments dropped).  read(file name) -> bytes overrides reading
+    the working tree (e.g. to hash a committed version)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2103_00154_gb300", "csrc")
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[name] + ["dsg_kernels.cuh", "dsg_common.cuh"]:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        if read is not None:
+            data = read(f)
+        else:
+            with open(os.path.join(csrc, f), "rb") as fh:
+                data = fh.read()
+        h.update(code_only(data))
     return h.hexdigest()[:16]
 
 
 def dram_traffic(workload: str, name: str):
     """DRAM bytes (read + write) of one launch of `name` from the last ncu
     capture recorded in profiles/dram_traffic.json, or None when there is none
-    or the kernel's sources changed since it was taken."""
+    or the kernel's code (comments aside) changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:

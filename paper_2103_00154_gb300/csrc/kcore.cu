@@ -129,7 +129,7 @@ struct CoreArgs {
     uint32_t local_max;   // rows up to this length found while draining stay in the block
     uint32_t local_work;  // ... while the block's local entries per batch stay within this
     uint32_t inline_max;  // rows up to this length claimed by a block's scan are drained by that block
-    uint64_t* trace;      // nullable: block 0 stamps (%globaltimer, kind) after every barrier
+    uint64_t* trace;      // nullable: block 0 stamps (%globaltimer, kind) at each phase end
     uint64_t trace_cap;
 };
 
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         const uint32_t tag = (uint32_t)(level + 1);
         CoreLevel* P = &ctl->lvl[level % 3];
         if (blockIdx.x == 0 && tid == 0) {
-            CoreLevel* R = &ctl->lvl[(level + 1) % 3];  // last read two barriers ago, next used after this level
+            CoreLevel* R = &ctl->lvl[(level + 1) % 3];  // last read at level - 2, next used at level + 1
             R->pending = gridDim.x;
             R->tail = 0;
             R->claimed = 0;
@@ -721,9 +721,10 @@ extern "C" dsg_status dsg_kcore_stats(const dsg_graph* g, uint32_t* out_core, ui
     return run_kcore(g, out_core, stats, nstats);
 }
 
-// Level timestamps of one core decomposition (debug/analysis): pairs
-// (%globaltimer, kind << 32 | k) after every grid barrier; kind 0 = start,
-// 1 = init, 2 = level scan, 3 = drain sub-round.  *count = pairs taken.
+// Phase timestamps of one core decomposition (debug/analysis): pairs
+// (%globaltimer, kind << 32 | k) as the kernel's trace stamps them (kind 0
+// start, 1 degrees initialised, 2 level over, 3/4/5 block 0's phases, then
+// per level the five (value, kind) pairs 6..10).  *count = pairs taken.
 extern "C" dsg_status dsg_debug_kcore_trace(const dsg_graph* g, uint64_t* ts, uint64_t cap, uint64_t* count) {
     clear_error();
     DSG_CHECK_ARG(g && ts && cap >= 2, "graph/ts/cap");
