@@ -274,50 +274,25 @@ __device__ __forceinline__ int hot_find(const HotTable& t, uint32_t x) {
 
 // count: one per endpoint of every non-loop pair; hot endpoints are counted
 // in shared memory and also recorded per block (blk[block * kHotMax + h]).
-// Each count's old value is the endpoint's slot in its row (for a hot
-// endpoint: in this block's range of the row), kept in slot[i] so the
-// scatter needs no atomics.  kPairU pairs per thread are in flight at once.
-constexpr uint32_t kPairU = 4;
-
 __global__ void __launch_bounds__(256) count_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
                                                     const uint32_t* __restrict__ dst, uint32_t* __restrict__ cnt,
                                                     const uint32_t* __restrict__ hot_ids,
                                                     const uint32_t* __restrict__ hot_n_p, uint32_t* __restrict__ blk,
-                                                    uint2* __restrict__ slot, IngestCtl* ctl) {
+                                                    IngestCtl* ctl) {
     __shared__ HotTable t;
     const uint32_t hot_n = *hot_n_p;
     hot_build(t, hot_ids, hot_n);
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m_raw; i0 += kPairU * stride) {
-        uint32_t u[kPairU], v[kPairU];
-#pragma unroll
-        for (uint32_t k = 0; k < kPairU; ++k) {
-            const uint64_t i = i0 + k * stride;
-            u[k] = v[k] = 0;
-            if (i < m_raw) {
-                u[k] = src[i];
-                v[k] = dst[i];
-            }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_raw;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = src[i], v = dst[i];
+        if (u >= n || v >= n) {
+            atomicOr(&ctl->err, ERR_RANGE);
+            continue;
         }
-        uint2 sl[kPairU];
-#pragma unroll
-        for (uint32_t k = 0; k < kPairU; ++k) {
-            const uint64_t i = i0 + k * stride;
-            if (i >= m_raw) continue;
-            if (u[k] >= n || v[k] >= n) {
-                atomicOr(&ctl->err, ERR_RANGE);
-                continue;
-            }
-            if (u[k] == v[k]) continue;
-            const int hu = hot_find(t, u[k]), hv = hot_find(t, v[k]);
-            sl[k].x = hu >= 0 ? atomicAdd(&t.local[hu], 1u) : atomicAdd(&cnt[u[k]], 1u);
-            sl[k].y = hv >= 0 ? atomicAdd(&t.local[hv], 1u) : atomicAdd(&cnt[v[k]], 1u);
-        }
-#pragma unroll
-        for (uint32_t k = 0; k < kPairU; ++k) {
-            const uint64_t i = i0 + k * stride;
-            if (i < m_raw && u[k] < n && v[k] < n && u[k] != v[k]) slot[i] = sl[k];
-        }
+        if (u == v) continue;
+        int hu = hot_find(t, u), hv = hot_find(t, v);
+        if (hu >= 0) atomicAdd(&t.local[hu], 1u); else atomicAdd(&cnt[u], 1u);
+        if (hv >= 0) atomicAdd(&t.local[hv], 1u); else atomicAdd(&cnt[v], 1u);
     }
     __syncthreads();
     for (uint32_t h = threadIdx.x; h < hot_n; h += blockDim.x) {
@@ -345,50 +320,29 @@ __global__ void __launch_bounds__(256) hot_block_bases(const uint32_t* __restric
     }
 }
 
-// scatter: each pair into both rows at the slots count gave its endpoints;
-// a hot endpoint's slot is relative to its block's reserved range (same grid
-// and pair-to-block assignment as count_kernel).
+// scatter: each pair into both rows; hot rows at the block's reserved range
+// (same grid and pair-to-block assignment as count_kernel).
 __global__ void __launch_bounds__(256) scatter_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
                                                       const uint32_t* __restrict__ dst,
-                                                      const uint64_t* __restrict__ start,
+                                                      const uint64_t* __restrict__ start, uint32_t* __restrict__ fill,
                                                       const uint32_t* __restrict__ hot_ids,
                                                       const uint32_t* __restrict__ hot_n_p,
-                                                      const uint32_t* __restrict__ blk, const uint2* __restrict__ slot,
-                                                      uint32_t* __restrict__ tmp) {
+                                                      const uint32_t* __restrict__ blk, uint32_t* __restrict__ tmp) {
     __shared__ HotTable t;
     const uint32_t hot_n = *hot_n_p;
     hot_build(t, hot_ids, hot_n);
     const uint32_t* myblk = blk + (uint64_t)blockIdx.x * kHotMax;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m_raw; i0 += kPairU * stride) {
-        uint32_t u[kPairU], v[kPairU];
-        uint2 sl[kPairU];
-        bool ok[kPairU];
-#pragma unroll
-        for (uint32_t k = 0; k < kPairU; ++k) {
-            const uint64_t i = i0 + k * stride;
-            ok[k] = false;
-            if (i < m_raw) {
-                u[k] = src[i];
-                v[k] = dst[i];
-                ok[k] = u[k] < n && v[k] < n && u[k] != v[k];
-                if (ok[k]) sl[k] = slot[i];
-            }
-        }
-        uint64_t su[kPairU], sv[kPairU];
-#pragma unroll
-        for (uint32_t k = 0; k < kPairU; ++k) {
-            if (!ok[k]) continue;
-            su[k] = start[u[k]];
-            sv[k] = start[v[k]];
-        }
-#pragma unroll
-        for (uint32_t k = 0; k < kPairU; ++k) {
-            if (!ok[k]) continue;
-            const int hu = hot_find(t, u[k]), hv = hot_find(t, v[k]);
-            tmp[su[k] + (hu >= 0 ? myblk[hu] : 0u) + sl[k].x] = v[k];
-            tmp[sv[k] + (hv >= 0 ? myblk[hv] : 0u) + sl[k].y] = u[k];
-        }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_raw;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = src[i], v = dst[i];
+        if (u >= n || v >= n || u == v) continue;
+        const int hu = hot_find(t, u), hv = hot_find(t, v);
+        const uint64_t pu = hu >= 0 ? start[u] + myblk[hu] + atomicAdd(&t.local[hu], 1u)
+                                    : start[u] + atomicAdd(&fill[u], 1u);
+        const uint64_t pv = hv >= 0 ? start[v] + myblk[hv] + atomicAdd(&t.local[hv], 1u)
+                                    : start[v] + atomicAdd(&fill[v], 1u);
+        tmp[pu] = v;
+        tmp[pv] = u;
     }
 }
 
@@ -825,9 +779,7 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     } else {
         DSG_TRY_CUDA(cudaMemsetAsync(hot_n, 0, 4, s));
     }
-    uint2* slot;  // each pair's slots in its two rows, from count for scatter
-    DSG_TRY_CUDA(sc.get(&slot, m_raw ? (size_t)m_raw : 1));
-    { LaunchScope ls_("ingest_count_kernel", s); count_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, cnt, hot_ids, hot_n, blk, slot, ctl); }
+    { LaunchScope ls_("ingest_count_kernel", s); count_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, cnt, hot_ids, hot_n, blk, ctl); }
     DSG_TRY_CUDA(cudaGetLastError());
     if (hot_pass) {
         LaunchScope ls_("ingest_hot_bases", s);
@@ -854,8 +806,8 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     }
     DSG_TRY_CUDA(sc.get(&tmp, total ? total : 1));
     DSG_TRY_CUDA(sc.get(&lists.rows, nlist ? nlist : 1));
-    DSG_TRY_CUDA(cudaMemsetAsync(newlen, 0, ((size_t)n + 1) * 4, s));  // the row sorts write every row's length
-    { LaunchScope ls_("ingest_scatter_kernel", s); scatter_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, start, hot_ids, hot_n, blk, slot, tmp); }
+    DSG_TRY_CUDA(cudaMemsetAsync(newlen, 0, ((size_t)n + 1) * 4, s));  // reused as the fill counter
+    { LaunchScope ls_("ingest_scatter_kernel", s); scatter_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, start, newlen, hot_ids, hot_n, blk, tmp); }
     DSG_TRY_CUDA(cudaGetLastError());
     {
         LaunchScope ls_("ingest_sort_small_rows", s);
