@@ -162,18 +162,30 @@ __global__ void __launch_bounds__(256) hot_gather(uint64_t m_raw, const uint32_t
     }
 }
 
-// One block: count endpoint frequencies over the gathered sample.
+// Endpoint frequencies over the gathered sample, split over kHotParts blocks
+// by a hash of the id (every block reads the whole sample and counts only its
+// own part, so no id is counted twice and the hashing work is shared).  Each
+// block lists its ids with at least kHotMinHits hits as (id, hits capped at
+// 255) and adds them to a histogram of the hit counts.
+constexpr uint32_t kHotParts = 8;
+
+__device__ __forceinline__ uint32_t hot_part(uint32_t x) { return (x * 0x9E3779B1u) >> 29; }  // 3 bits
+__device__ __forceinline__ uint32_t sample_slot(uint32_t x) { return (x * 0x85EBCA6Bu) >> 19; }  // 13 bits
+
 __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, const uint2* __restrict__ sample,
-                                                   uint32_t* __restrict__ hot_ids, uint32_t* __restrict__ hot_n) {
+                                                   uint2* __restrict__ cand, uint32_t* __restrict__ cand_n,
+                                                   uint32_t* __restrict__ hist) {
     extern __shared__ uint32_t sample_smem[];  // kSampleSlots keys, then kSampleSlots counts
     uint32_t* key = sample_smem;
     uint32_t* cnt = sample_smem + kSampleSlots;
-    __shared__ uint32_t nsel;
+    __shared__ uint32_t lhist[256];
+    __shared__ uint32_t nq, base, fill;
     for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x) {
         key[i] = kHotEmpty;
         cnt[i] = 0;
     }
-    if (threadIdx.x == 0) nsel = 0;
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) lhist[i] = 0;
+    if (threadIdx.x == 0) nq = fill = 0;
     __syncthreads();
     const uint64_t take = sample_take(m_raw);
     constexpr uint32_t kU = 8;  // pairs loaded per thread before any is counted
@@ -192,8 +204,8 @@ __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, c
 #pragma unroll
         for (uint32_t t = 0; t < 2 * kU; ++t) {
             const uint32_t x = e[t];
-            if (x >= n || e[t ^ 1u] == x) continue;  // out of range, padding or a loop
-            uint32_t h = (x * 0x9E3779B1u) >> 19;  // 13 bits
+            if (x >= n || e[t ^ 1u] == x || hot_part(x) != blockIdx.x) continue;  // padding, a loop, another part
+            uint32_t h = sample_slot(x);
             for (uint32_t probe = 0; probe < 8; ++probe, h = (h + 1) & (kSampleSlots - 1)) {
                 const uint32_t cur = key[h];
                 const uint32_t prev = cur == x ? x : (cur == kHotEmpty ? atomicCAS(&key[h], kHotEmpty, x) : cur);
@@ -205,31 +217,43 @@ __global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, c
         }
     }
     __syncthreads();
-    // keep the most frequent: a histogram of the hit counts (capped at 255)
-    // gives the count above which all fit, and the boundary count fills the rest
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t cut, room, extra;
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x)
+        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) {
+            atomicAdd(&lhist[min(cnt[i], 255u)], 1u);
+            atomicAdd(&nq, 1u);
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) base = nq ? atomicAdd(cand_n, nq) : 0u;
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x)
+        if (lhist[i]) atomicAdd(&hist[i], lhist[i]);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x)
-        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) atomicAdd(&hist[min(cnt[i], 255u)], 1u);
-    __syncthreads();
+        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) cand[base + atomicAdd(&fill, 1u)] = make_uint2(key[i], min(cnt[i], 255u));
+}
+
+// Keep the most frequent candidates: the histogram of their hit counts gives
+// the count above which all fit in kHotMax, and the boundary count fills the rest.
+__global__ void __launch_bounds__(1024) hot_select(const uint2* __restrict__ cand, const uint32_t* __restrict__ cand_n,
+                                                   const uint32_t* __restrict__ hist, uint32_t* __restrict__ hot_ids,
+                                                   uint32_t* __restrict__ hot_n) {
+    __shared__ uint32_t cut, room, extra, nsel;
     if (threadIdx.x == 0) {
         uint32_t acc = 0, b = 255;
         while (b >= kHotMinHits && acc + hist[b] <= kHotMax) acc += hist[b--];
         cut = b;                // buckets above cut are taken whole
         room = kHotMax - acc;  // slots left for bucket cut
         extra = 0;
+        nsel = 0;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x) {
-        if (key[i] == kHotEmpty || cnt[i] < kHotMinHits) continue;
-        const uint32_t bk = min(cnt[i], 255u);
-        bool take = bk > cut;
-        if (!take && bk == cut) take = atomicAdd(&extra, 1u) < room;
+    const uint32_t nc = *cand_n;
+    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+        const uint2 c = cand[i];
+        bool take = c.y > cut;
+        if (!take && c.y == cut) take = atomicAdd(&extra, 1u) < room;
         if (take) {
             const uint32_t at = atomicAdd(&nsel, 1u);
-            if (at < kHotMax) hot_ids[at] = key[i];
+            if (at < kHotMax) hot_ids[at] = c.x;
         }
     }
     __syncthreads();
@@ -775,7 +799,19 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
             LaunchScope ls_("ingest_hot_gather", s);
             hot_gather<<<(uint32_t)((sample_take(m_raw) + 255) / 256), 256, 0, s>>>(m_raw, src, dst, sample);
         }
-        { LaunchScope ls_("ingest_hot_sample", s); hot_sample<<<1, 1024, smem, s>>>(n, m_raw, sample, hot_ids, hot_n); }
+        uint2* cand;         // (id, hits) of the frequent sampled endpoints, every part's
+        uint32_t* cand_cnt;  // [0, 256) histogram of their hits, [256] their number
+        DSG_TRY_CUDA(sc.get(&cand, (size_t)kHotParts * kSampleSlots));
+        DSG_TRY_CUDA(sc.get(&cand_cnt, 257));
+        DSG_TRY_CUDA(cudaMemsetAsync(cand_cnt, 0, 257 * sizeof(uint32_t), s));
+        {
+            LaunchScope ls_("ingest_hot_sample", s);
+            hot_sample<<<kHotParts, 1024, smem, s>>>(n, m_raw, sample, cand, cand_cnt + 256, cand_cnt);
+        }
+        {
+            LaunchScope ls_("ingest_hot_select", s);
+            hot_select<<<1, 1024, 0, s>>>(cand, cand_cnt + 256, cand_cnt, hot_ids, hot_n);
+        }
     } else {
         DSG_TRY_CUDA(cudaMemsetAsync(hot_n, 0, 4, s));
     }
