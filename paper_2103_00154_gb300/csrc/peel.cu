@@ -20,6 +20,8 @@
 //
 // Vertex state is one 32-bit word: an alive vertex holds its degree inside
 // S_r (< 2^31); a failed one holds 0x80000000 | (round it failed, 1-based).
+#include <algorithm>
+#include <cstdlib>
 #include <string>
 #include <thread>
 
@@ -420,7 +422,8 @@ dsg_status dsg_solve(const dsg_graph* g, uint32_t count, const uint32_t* eps_num
     // graph's size class say the core numbers dominate, run one after the
     // other with the whole GPU each
     double peel_ms = 0, core_ms = 0;
-    const bool mostly_core = tuned_times(g, &peel_ms, &core_ms) && count * peel_ms < 0.25 * core_ms;
+    const bool tuned = tuned_times(g, &peel_ms, &core_ms);
+    const bool mostly_core = tuned && count * peel_ms < 0.25 * core_ms;
     if (count == 0 || !out_core || g->n == 0 || mostly_core) {
         dsg_status st = peels(g);
         if (st != DSG_OK || !out_core) return st;
@@ -453,7 +456,18 @@ dsg_status dsg_solve(const dsg_graph* g, uint32_t count, const uint32_t* eps_num
     va.stream = sa;
     vb.stream = sb;
     va.force_block = vb.force_block = 1024;
-    va.max_blocks = sms / 2 > 0 ? sms / 2 : 1;
+    // the peels' share of the SMs: DSG_SOLVE_PEEL_PERMILLE if set, else from
+    // the autotuned times (each side's share of the summed time, within
+    // [1/4, 3/4]), else half
+    double peel_frac = 0.5;
+    if (tuned && count * peel_ms + core_ms > 0)
+        peel_frac = std::min(0.75, std::max(0.25, count * peel_ms / (count * peel_ms + core_ms)));
+    if (const char* e = getenv("DSG_SOLVE_PEEL_PERMILLE")) {
+        const long pm = strtol(e, nullptr, 10);
+        if (pm > 0 && pm < 1000) peel_frac = pm / 1000.0;
+    }
+    va.max_blocks = std::max<uint32_t>(1, (uint32_t)(sms * peel_frac + 0.5));
+    if (va.max_blocks >= sms) va.max_blocks = sms > 1 ? sms - 1 : 1;
     vb.max_blocks = sms - va.max_blocks > 0 ? sms - va.max_blocks : 1;
     dsg_status st_core = DSG_OK;
     std::string err_core;
