@@ -411,10 +411,12 @@ void dsg_set_allocator(dsg_alloc_fn alloc, dsg_free_fn free_fn, void* ctx);
  * numbers of one graph in one call: the same results as count dsg_bahmani
  * calls plus one dsg_kcore call (out_sets[i], out_E[i], out_V[i]; out_core),
  * with the peels and the core decomposition running side by side on two
- * internal streams, each on half of the SMs -- unless the autotuned times of
- * the graph's size class show the core numbers taking over four times as
- * long as the peels, in which case they run one after the other on the whole
- * GPU.  Results never depend on the choice.  out_sets (and its entries),
+ * internal streams, the peels on the share of the SMs that their autotuned
+ * time has in the summed time (within 1/4 and 3/4; half when the graph's size
+ * class is not tuned; the environment variable DSG_SOLVE_PEEL_PERMILLE, 1..999,
+ * overrides it) -- unless the autotuned times show the core numbers taking
+ * over four times as long as the peels, in which case they run one after the
+ * other on the whole GPU.  Results never depend on the choice.  out_sets (and its entries),
  * out_E, out_V nullable; out_core NULL runs the peels only.  Work starts
  * after what is queued on the graph's stream, which waits for all of it
  * before the call returns.  No counterpart in the paper (its two algorithms
