@@ -317,15 +317,17 @@ dsg_status dsg_get_tuning(uint32_t* block, uint32_t* blocks_per_sm, uint32_t* sh
 dsg_status dsg_set_hot_degree(uint32_t hot_deg);
 /* Core numbers: a vertex whose row has at most local_max entries and that
  * reaches the current level while a block drains is drained by that block
- * in the same sub-round (PKC's thread-local buffer), as long as the block's
- * local entries in that sub-round stay within local_work; other vertices go
- * to the grid-wide frontier of the next sub-round.  Defaults 1024 / 16384;
- * DSG_LOCAL_MAX, DSG_LOCAL_WORK.  Results never depend on them. */
+ * from a shared-memory queue (PKC's thread-local buffer), as long as the
+ * entries the block takes on this way stay within local_work (for its own
+ * rows of the level, and again for each batch of queue pieces it takes);
+ * other rows go to the level-wide queue of row pieces that every block
+ * drains.  Defaults 1024 / 16384; DSG_LOCAL_MAX, DSG_LOCAL_WORK.  Results
+ * never depend on them. */
 dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work);
 /* Core numbers: a vertex whose row has at most inline_max entries and that a
- * block's level scan finds at the level is drained by that block in the same
- * sub-round; longer rows are spread over every warp in the next sub-round.
- * Default 4096; DSG_INLINE_MAX.  Results never depend on it. */
+ * block's level scan claims is drained by that block; longer rows go to the
+ * level-wide queue in pieces of at most chunk_len entries, which every block
+ * takes from.  Default 4096; DSG_INLINE_MAX.  Results never depend on it. */
 dsg_status dsg_set_inline_max(uint32_t inline_max);
 
 /*
