@@ -110,6 +110,14 @@ def test_rows_spread_far_apart(n, gap):
     check_all(inputs.from_pairs(n, pairs), tag=f"spread n={n} gap={gap}")
 
 
+def test_leaves_past_the_search_pass_bound():
+    # a star with leaves 900 ids apart plus a triangle: the histogram walker's
+    # steps over the leaf rows need more than 64 coarse-sample passes
+    leaves = np.arange(900, 200_000, 900, dtype=np.int64)
+    pairs = np.concatenate([np.stack([np.zeros_like(leaves), leaves], 1), [[1, 2], [2, 3], [1, 3]]])
+    check_all(inputs.from_pairs(200_000, pairs), tag="far leaves")
+
+
 def test_supplied_values_host_device_and_global_histogram():
     raw = inputs.er_block(n=9000, m=40000, k=60, p=0.5, seed=7)
     c = oracle.from_raw(raw)

@@ -160,6 +160,11 @@ def spread_rows_cases():
         for t in range(1, int(rng.integers(1, 61)) + 1):
             pairs.append((c0, c0 + t))
     out.append(inputs.from_pairs(200_000, pairs, "far_stars"))
+    # one star whose 222 leaves are 900 ids apart: a walker step over the
+    # one-entry leaf rows spans ~115,000 rows, past the 64-pass bound of the
+    # coarse-sample search, so the plain binary search places the rest
+    leaves = np.arange(900, 200_000, 900, dtype=np.int64)
+    out.append(inputs.from_pairs(200_000, np.stack([np.zeros_like(leaves), leaves], 1), "far_leaves"))
     return out
 
 
