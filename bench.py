@@ -8,10 +8,10 @@ One step = the whole hot path over one synthetic graph:
 Metric: adjacency entries scanned per second (each solve reads every row
 once: 2m entries per peel and per core decomposition), bit-exact outputs.
 
-Default workload: R-MAT scale 20 (2^20 vertices, 2^24 generated pairs,
-a=.57 b=.19 c=.19, seed 1), eps in {1/1000, 1/10, 1}.  Inputs are resident in
-HBM before the timed region; L2 is flushed (a 512 MiB write) before every
-timed step.
+Default workload: Chung-Lu n = 2^24, exponent 2.1, mean degree 32, max
+expected degree 100,000, seed 2, 2^28 generated pairs (the largest
+single-graph configuration), eps = 1/10.  Inputs are resident in HBM before
+the timed region; L2 is flushed (a 512 MiB write) before every timed step.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the same workload instead (the reference arm of this project).
@@ -69,6 +69,33 @@ WORKLOADS = {
         eps=[(1, 10)]),
 }
 
+# The serial oracle needs minutes for one whole step of the largest graphs, so
+# its timed leg runs on a bounded sample: the same generator at a smaller
+# scale (same exponent, mean degree and seed; max expected degree halved per
+# factor 4 in n, as between the 2^24 and 2^22 shapes).  Workloads not listed
+# here are timed on themselves.
+CL_SAMPLE = dict(
+    desc="Chung-Lu n=1,048,576, exponent 2.1, mean degree 32, max expected degree 25,000, seed 2, 2^24 "
+         "generated pairs (the same generator at 1/16 of the vertices and pairs)",
+    gen=lambda: inputs.chung_lu(n=1 << 20, m_draws=1 << 24, gamma=2.1, mean=32.0, wmax=2.5e4, seed=2))
+CPU_SAMPLES = {"cl24": CL_SAMPLE, "cl22": CL_SAMPLE}
+
+
+def cpu_sample(workload: str, raw=None):
+    """(raw graph, description) the oracle legs time for `workload`."""
+    smp = CPU_SAMPLES.get(workload)
+    if smp is None:
+        return (raw if raw is not None else WORKLOADS[workload]["gen"]()), "the workload itself"
+    return smp["gen"](), smp["desc"]
+
+
+def workload_config(workload: str, n: int, m_raw: int, world: int) -> dict:
+    """The `config` object of a JSON line: what identifies the workload, the
+    same for both arms."""
+    return {"workload": workload, "desc": WORKLOADS[workload]["desc"], "n": int(n), "m_raw": int(m_raw),
+            "l2": "flushed before every timed step (512 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -80,7 +107,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat20")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cl24")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cbds", action="store_true", help="skip the densest-core / CBDS-P timing")
@@ -188,15 +215,33 @@ def peel_bytes(n: int, m: int, st: dict) -> int:
     return (8 * m + 16 * n + 4 * n + 8 * sum_S - 4 * n + 4 * sum_S1 + 4 * 2 * m + 4 * st["decrements"])
 
 
-def kcore_bytes(n: int, m: int, st: dict) -> int:
-    """Algorithmic bytes of one core-number launch: adjacency 8m; offsets of
-    every frontier vertex 16n; degree init write 4n and claim-bitmap clear
-    n/8; per level the remaining id, degree and claim word read 12|R_k|
-    (level 0 reads no id); one claim atomic per vertex 4n; each degree atomic
-    (one decrement per adjacency entry, and the undos) reads and writes 4 B;
-    remaining-list writes 4 B each."""
-    return (8 * m + 16 * n + 4 * n + n // 8 + 12 * st["rem_scanned"] - 4 * n + 4 * n
-            + 8 * st["atomics"] + 4 * st["rem_written"])
+def kcore_pkc_atomics(m: int, sum_core: int) -> int:
+    """Degree atomics of Algorithm 2's first phase run serially: a neighbour
+    above the level loses one degree, and every vertex ends at its core
+    number, so the decrements number sum(deg - core) = 2m - sum(core)."""
+    return 2 * m - sum_core
+
+
+def kcore_bytes(n: int, m: int, st: dict, sum_core: int) -> int:
+    """Algorithmic bytes of one core-number launch (the method's own traffic):
+    adjacency 8m; two offsets per drained vertex 16n; the core number write
+    4n; per level the remaining id and degree read 8|R_k| (level 0 reads no
+    id); one degree read per adjacency entry 4 * 2m; a read and a write for
+    each of the method's decrements 8 * (2m - sum(core))."""
+    return (8 * m + 16 * n + 4 * n + 8 * st["rem_scanned"] - 4 * n + 4 * 2 * m
+            + 8 * kcore_pkc_atomics(m, sum_core))
+
+
+def kcore_overhead_bytes(n: int, m: int, st: dict, sum_core: int) -> dict:
+    """Traffic the kernel's schedule adds beyond kcore_bytes: the claim
+    bitmap (clear n/8, a claim word read per scanned vertex, one claim
+    atomic per vertex), the remaining-list writes, and the atomics above the
+    method's count (the kernel decrements every neighbour first and undoes
+    the decrement below the level, instead of reading first)."""
+    extra_atomics = st["atomics"] - kcore_pkc_atomics(m, sum_core)
+    return {"extra_atomics": int(extra_atomics), "bytes": int(n // 8 + 4 * st["rem_scanned"] + 8 * n
+                                                               + 4 * st["rem_written"] + 8 * extra_atomics
+                                                               - 4 * 2 * m)}
 
 
 KERNEL_SOURCES = {
@@ -351,7 +396,9 @@ def run_ours(args, wl, raw, rank, world):
         tr = g.bahmani_trace(p, q)
         peel_stats.append({"sum_S": int(tr.hist_S[:-1].sum()), "decrements": int(tr.decrements),
                            "rounds": tr.rounds})
-    _, kst = g.kcore_counters()
+    core_h, kst = g.kcore_counters()
+    sum_core = int(core_h.astype(np.int64).sum())
+    del core_h
     g.close()
 
     events = []
@@ -391,7 +438,7 @@ def run_ours(args, wl, raw, rank, world):
             per_launch = [peel_bytes(n, m, s) for s in peel_stats]
             alg = sum(per_launch) / len(per_launch)
         elif name == "kcore_levels":
-            alg = kcore_bytes(n, m, kst)
+            alg = kcore_bytes(n, m, kst, sum_core)
         else:
             continue
         avg_s = ms / cnt / 1e3
@@ -400,6 +447,9 @@ def run_ours(args, wl, raw, rank, world):
                            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                            "traffic": dram_traffic(args.workload, name), "alg_bytes_per_launch": int(alg),
                            "avg_launch_ms": round(ms / cnt, 4)}
+        if name == "kcore_levels":
+            by_kernel[name]["schedule_overhead"] = kcore_overhead_bytes(n, m, kst, sum_core)
+            by_kernel[name]["method_atomics"] = kcore_pkc_atomics(m, sum_core)
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = by_kernel.get(top[0]) if top else None
     shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()} if prof else {}
@@ -417,7 +467,7 @@ def run_ours(args, wl, raw, rank, world):
         "clocks": clk.summary(),
         "wall_s": t_wall,
         "peel_rounds": [s["rounds"] for s in peel_stats],
-        "kcore": kst,
+        "kcore": dict(kst, sum_core=sum_core),
         "tuning": tuning,
     }
 
@@ -695,43 +745,59 @@ def oracle_step(raw, eps):
     return c.m
 
 
-def run_cpu_baseline(wl, raw, seconds):
+def run_cpu_baseline(args, wl, raw, seconds):
     """The oracle as it stands, serial on one host core, on whole steps of
-    the same workload until about `seconds` of CPU time have passed."""
+    the workload's CPU sample (ingest + the workload's peels + core numbers)
+    until about `seconds` of CPU time have passed."""
+    smp, smp_desc = cpu_sample(args.workload, raw)
     t0 = time.perf_counter()
     steps = 0
     m = 0
     while True:
-        m = oracle_step(raw, wl["eps"])
+        m = oracle_step(smp, wl["eps"])
         steps += 1
         if time.perf_counter() - t0 >= seconds or steps >= 50:
             break
     dt = time.perf_counter() - t0
     eps_step = 2 * m * (len(wl["eps"]) + 1)
     return {"value": eps_step * steps / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} whole step(s) of the workload (ingest + {len(wl['eps'])} peel(s) + core numbers), "
+            "sample": f"{steps} whole step(s) (ingest + {len(wl['eps'])} peel(s) + core numbers) of {smp_desc}, "
                       f"{dt:.1f} s, serial C oracle"}
 
 
-def run_reference(args, wl, raw):
-    import oracle
-    small = inputs.er_block(n=10_000, m=50_000, k=100, p=0.5, seed=0)
+def run_reference(args, wl):
+    """The reference arm: the serial C oracle (there is no reference
+    implementation; the paper holds no code) on the host cores, each step one
+    whole step of the workload's CPU sample."""
+    smp, smp_desc = cpu_sample(args.workload)
     for _ in range(max(args.warmup, 0)):
-        oracle_step(small, wl["eps"])
+        oracle_step(inputs.er_block(n=10_000, m=50_000, k=100, p=0.5, seed=0), wl["eps"])
     t0 = time.perf_counter()
     m = 0
     for _ in range(args.steps):
-        m = oracle_step(raw, wl["eps"])
+        m = oracle_step(smp, wl["eps"])
     dt = time.perf_counter() - t0
     eps_step = 2 * m * (len(wl["eps"]) + 1)
     value = eps_step * args.steps / dt
+    n_full, m_raw_full = workload_size(args.workload)
     return {"impl": "reference", "metric": "edges scanned/s", "value": value, "unit": "edges/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": args.workload, "desc": wl["desc"]},
+            "data": "synthetic", "config": workload_config(args.workload, n_full, m_raw_full,
+                                                           int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} whole step(s) of the workload, warm-up on the 1e4-vertex case"},
+                             "sample": f"each step one whole step (ingest + {len(wl['eps'])} peel(s) + core "
+                                       f"numbers) of {smp_desc}; warm-up on the 10^4-vertex case"},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def workload_size(workload: str):
+    """(n, generated pairs) of a single-graph workload, without generating it."""
+    sizes = {"cl24": (1 << 24, 1 << 28), "cl22": (1 << 22, 1 << 26), "rmat20": (1 << 20, 1 << 24)}
+    if workload in sizes:
+        return sizes[workload]
+    raw = WORKLOADS[workload]["gen"]()
+    return raw.n, raw.m_raw
 
 
 def main():
@@ -742,8 +808,11 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        raw = wl["gen"]()
-        print(json.dumps(run_reference(args, wl, raw)), flush=True)
+        if wl.get("kind"):
+            print(json.dumps({"impl": "reference", "unavailable": f"the {args.workload} workload has no oracle "
+                              "arm; the single-graph workloads do"}), flush=True)
+            return 0
+        print(json.dumps(run_reference(args, wl)), flush=True)
         return 0
 
     import torch
@@ -795,7 +864,7 @@ def main():
     res = run_ours(args, wl, raw, rank, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = run_cpu_baseline(wl, raw, args.cpu_seconds)
+        cpu = run_cpu_baseline(args, wl, raw, args.cpu_seconds)
     if rank == 0:
         line = {
             "metric": "edges scanned/s",
@@ -810,11 +879,10 @@ def main():
             "vs_baseline": None,
             "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "n": raw.n, "m_raw": raw.m_raw,
-                       "m": res["m"], "edges_scanned_per_step": res["edges_per_step"],
-                       "l2": "flushed before every timed step (512 MiB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "step": {"device_timed": "dsg_graph_from_edges, then " + (
+            "config": workload_config(args.workload, raw.n, raw.m_raw, world),
+            "m": res["m"],
+            "edges_scanned_per_step": res["edges_per_step"],
+            "run": {"step": {"device_timed": "dsg_graph_from_edges, then " + (
                                     "one dsg_bahmani per eps and dsg_kcore, each kernel bracketed by timing events"
                                     if args.step_api == "separate" else
                                     "dsg_solve (peels and core numbers side by side), each kernel bracketed by "

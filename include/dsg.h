@@ -160,18 +160,23 @@ uint64_t dsg_round_bound(uint32_t n, uint32_t eps_num, uint32_t eps_den);
  *   n, off, adj  canonical CSR in DEVICE memory (as dsg_graph_from_csr)
  *   out_set      nullable, n bytes of DEVICE memory
  *   out_E/out_V  nullable host pointers
- *   stream       cudaStream_t to run on (NULL: default stream); the call
- *                synchronises it before returning
- * Limits: the scratch needs 16n bytes (alive lists, state, failed list) plus
- * 8(n + 2m/chunk_len + 1) bytes (chunk items, chunk_len 256 by default) plus
- * 16 * (dsg_round_bound(n, p, q) + 1) bytes (round history); a graph that
- * needs more than 64 MiB is rejected with DSG_EINVAL before any GPU work
- * (with eps > 0 that admits n up to about 2.7 million at m = 8n).
- * The first call on a device looks the buffer's address up (once per
- * device, with that device current); make that first call before any CUDA
- * stream capture.  All calls share the one buffer and it keeps the last
- * call's contents: calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.
+ *   stream       cudaStream_t to run on (NULL: default stream).  Every call
+ *                waits for this stream twice: it reads off[n] back before
+ *                the launch and the results after it.
+ * Limits: the scratch is eight arrays, each rounded up to a multiple of 256
+ * bytes: four of 4n bytes (vertex state, two alive lists, failed list), the
+ * chunk items 8(n + 2m/chunk_len + 1) bytes, two round histories of
+ * 8(dsg_round_bound(n, p, q) + 1) bytes, and a control block of about 1 KB;
+ * chunk_len is the current tuning's (dsg_set_tuning; 256 by default).  A
+ * graph whose scratch exceeds 64 MiB is rejected with DSG_EINVAL before any
+ * GPU work (with eps > 0 and the default chunk_len that admits n up to about
+ * 2.7 million at m = 8n).
+ * The first call in each CUDA context (the first on a device, and the first
+ * after that device's context was destroyed and made again) looks the
+ * buffer's device address up, with the device current; make that first call
+ * before any CUDA stream capture.  All calls share the one buffer and it
+ * keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
  */
 dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const uint32_t* adj, uint32_t eps_num,
                                uint32_t eps_den, uint8_t* out_set, uint64_t* out_E, uint64_t* out_V, void* stream);
@@ -456,19 +461,10 @@ dsg_status dsg_debug_wait_timeout(uint32_t which, uint64_t limit_ns);
  *                          6/7 latest own / queue phase end over the blocks
  *                          (ns, as block 0 sees them), 8 claims, 9 claims by
  *                          the scan, 10 queued row pieces; *count = pairs
- *   dsg_debug_barrier_ns   average latency of one grid barrier of a
- *                          co-resident grid (block threads, blocks_per_sm,
- *                          0 = occupancy limit) over iters barriers
  */
 dsg_status dsg_debug_peel_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, uint64_t* ts, uint64_t cap,
                                 uint64_t* count);
 dsg_status dsg_debug_kcore_trace(const dsg_graph* g, uint64_t* ts, uint64_t cap, uint64_t* count);
-dsg_status dsg_debug_barrier_ns(uint32_t block, uint32_t blocks_per_sm, uint32_t iters, double* ns,
-                                uint32_t* grid_out);
-/* Throughput (1e9 ops/s) of `ops` random 4-byte accesses to a words-long
- * device array: mode 0 loads, 1 atomic adds without return, 2 atomic adds
- * returning the old value (the access patterns of the peel and core kernels). */
-dsg_status dsg_debug_random_access(uint32_t words, uint64_t ops, int mode, double* gops);
 
 /* ------------------------------------------------------- launch accounting */
 

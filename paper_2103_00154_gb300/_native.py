@@ -123,8 +123,6 @@ _SIGS = [
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),
     ("dsg_debug_peel_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, _U64P, c.c_uint64, _U64P]),
     ("dsg_debug_kcore_trace", c.c_int, [_VP, _U64P, c.c_uint64, _U64P]),
-    ("dsg_debug_random_access", c.c_int, [c.c_uint32, c.c_uint64, c.c_int, c.POINTER(c.c_double)]),
-    ("dsg_debug_barrier_ns", c.c_int, [c.c_uint32, c.c_uint32, c.c_uint32, c.POINTER(c.c_double), _U32P]),
     ("dsg_launch_count", c.c_ulonglong, []),
     ("dsg_profile_enable", None, [c.c_int]),
     ("dsg_profile_reset", None, []),

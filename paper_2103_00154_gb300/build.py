@@ -16,9 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdsg.so")
-# DSG_LIB_VARIANT=debug builds and loads a bounds-checked copy (libdsg_debug.so);
-# DSG_LIB_VARIANT=plainld one with plain adjacency loads (libdsg_plainld.so), for comparison
-VARIANTS = {"": [], "debug": ["-DDSG_DEBUG_BOUNDS"], "plainld": ["-DDSG_PLAIN_ADJ_LOADS"]}
+# DSG_LIB_VARIANT=debug builds and loads a bounds-checked copy (libdsg_debug.so)
+VARIANTS = {"": [], "debug": ["-DDSG_DEBUG_BOUNDS"]}
 
 
 def variant() -> str:

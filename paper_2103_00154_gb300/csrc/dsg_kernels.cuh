@@ -11,14 +11,7 @@ namespace dsg {
 // Adjacency entries are read once per solve: load them with the streaming
 // (evict-first) policy so they do not push the per-vertex state (degrees,
 // marks), which every entry looks up at random, out of L2.
-// (DSG_PLAIN_ADJ_LOADS builds the plain-load variant, for comparison.)
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
-#ifdef DSG_PLAIN_ADJ_LOADS
-    return *p;
-#else
-    return __ldcs(p);
-#endif
-}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
 
 // Tuning knobs of the round kernels (see tune.cu for the defaults and the
 // autotuner that picks them).

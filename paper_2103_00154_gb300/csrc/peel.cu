@@ -555,18 +555,55 @@ constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB per device
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, per device.  Host code may not use the
-// symbol itself as an address (on the host it names a shadow variable), so
-// the address is looked up once per device with cudaGetSymbolAddress.
+// Device address of g_noalloc_scratch.  Host code may not use the symbol
+// itself as an address (on the host it names a shadow variable), so the
+// address is looked up with cudaGetSymbolAddress, with the device current,
+// the first time a call runs in a CUDA context.  The cache is keyed on the
+// context's id, not on the device ordinal: after a context is destroyed and
+// made again (cudaDeviceReset, a released primary context) the module is
+// loaded again and the array may sit elsewhere, so the new context looks it
+// up afresh.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+struct NoAllocSlot {
+    unsigned long long ctx_id = 0;  // 0: empty
+    unsigned char* addr = nullptr;
+};
 static std::mutex g_noalloc_mu;
-static unsigned char* g_noalloc_addr[64];
+static NoAllocSlot g_noalloc_slots[64];
+
+// Id of the current context (0 when the driver cannot tell: the address is
+// then looked up on every call).
+static unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 static dsg_status noalloc_scratch(unsigned char** out) {
     int dev = 0;
     DSG_TRY_CUDA(cudaGetDevice(&dev));
     DSG_CHECK_ARG(dev >= 0 && dev < 64, "device ordinal above 63");
+    const unsigned long long id = current_ctx_id();
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    NoAllocSlot& slot = g_noalloc_slots[dev];
+    if (id == 0 || slot.ctx_id != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -574,9 +611,10 @@ static dsg_status noalloc_scratch(unsigned char** out) {
                       cudaGetErrorString(e));
             return DSG_ECUDA;
         }
-        g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+        slot.addr = static_cast<unsigned char*>(p);
+        slot.ctx_id = id;
     }
-    *out = g_noalloc_addr[dev];
+    *out = slot.addr;
     return DSG_OK;
 }
 
@@ -588,6 +626,7 @@ static cudaError_t launch_peel_noalloc(PeelArgs& a, uint32_t blocks_per_sm, cuda
     cudaError_t e = coop_grid(peel_kernel<TB>, TB, 0, a.n, blocks_per_sm, &grid);
     if (e != cudaSuccess) return e;
     void* params[] = {&a};
+    LaunchScope ls("peel_rounds", s);
     return cudaLaunchCooperativeKernel((const void*)peel_kernel<TB>, dim3(grid), dim3(TB), params, 0, s);
 }
 
@@ -665,7 +704,10 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     if (out_set) {
         uint64_t want = ((uint64_t)n + 255) / 256, cap_b = (uint64_t)dev_info().sms * 8;
         uint32_t blocks = (uint32_t)(want < cap_b ? want : cap_b);
-        peel_finish_kernel<<<blocks, 256, 0, s>>>(n, a.st, a.ctl, nullptr, out_set);
+        {
+            LaunchScope ls("peel_finish", s);
+            peel_finish_kernel<<<blocks, 256, 0, s>>>(n, a.st, a.ctl, nullptr, out_set);
+        }
         DSG_TRY_CUDA(cudaGetLastError());
     }
     PeelCtl c;

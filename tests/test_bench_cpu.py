@@ -29,11 +29,60 @@ def test_traffic_is_dropped_once_the_kernel_code_changes(tmp_path, monkeypatch):
     assert bench.dram_traffic("w", "kcore_levels") is None
 
 
-def test_kcore_byte_model_counts_each_atomic_read_and_write():
+def test_kcore_byte_model_follows_the_method():
     n, m = 10, 20
     st = {"rem_scanned": 30, "rem_written": 15, "atomics": 50}
-    base = bench.kcore_bytes(n, m, st)
-    st2 = dict(st, atomics=51)
-    assert bench.kcore_bytes(n, m, st2) - base == 8
-    st3 = dict(st, rem_written=16)
-    assert bench.kcore_bytes(n, m, st3) - base == 4
+    base = bench.kcore_bytes(n, m, st, sum_core=25)
+    # the kernel's own atomics and list writes are schedule overhead, not method bytes
+    assert bench.kcore_bytes(n, m, dict(st, atomics=51), 25) == base
+    assert bench.kcore_bytes(n, m, dict(st, rem_written=16), 25) == base
+    # each method decrement (2m - sum core) reads and writes 4 B; each scanned remaining vertex 8 B
+    assert bench.kcore_bytes(n, m, st, 24) - base == 8
+    assert bench.kcore_bytes(n, m, dict(st, rem_scanned=31), 25) - base == 8
+    ov = bench.kcore_overhead_bytes(n, m, st, 25)
+    assert ov["extra_atomics"] == 50 - (2 * m - 25)
+
+
+def _serial_level_peel_decrements(n, rows):
+    """Algorithm 2's first phase run by one thread: level k takes the vertices
+    of degree k, and a drained vertex takes one from each neighbour whose
+    degree is above k (a neighbour reaching k joins the level).  Returns the
+    core numbers and the number of decrements."""
+    deg = [len(r) for r in rows]
+    done = [False] * n
+    dec, visited, k = 0, 0, 0
+    while visited < n:
+        buf = [v for v in range(n) if not done[v] and deg[v] == k]
+        for v in buf:
+            done[v] = True
+        i = 0
+        while i < len(buf):
+            v = buf[i]
+            i += 1
+            for u in rows[v]:
+                if deg[u] > k:
+                    deg[u] -= 1
+                    dec += 1
+                    if deg[u] == k:
+                        done[u] = True
+                        buf.append(u)
+        visited += len(buf)
+        k += 1
+    return deg, dec
+
+
+def test_method_decrements_are_degree_minus_core():
+    import numpy as np
+    import inputs
+    for seed in range(6):
+        raw = inputs.random_small(40, 0.05 + 0.04 * seed, seed)
+        n = raw.n
+        rows = [set() for _ in range(n)]
+        for a, b in zip(raw.src.tolist(), raw.dst.tolist()):
+            if a != b:
+                rows[a].add(b)
+                rows[b].add(a)
+        rows = [sorted(r) for r in rows]
+        m = sum(len(r) for r in rows) // 2
+        core, dec = _serial_level_peel_decrements(n, rows)
+        assert dec == bench.kcore_pkc_atomics(m, int(np.sum(core)))

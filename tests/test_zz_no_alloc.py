@@ -57,6 +57,43 @@ def test_noalloc_matches_dsg_bahmani_on_consecutive_calls():
         np.testing.assert_array_equal(got_mask, want_mask)
 
 
+def test_noalloc_allocates_no_device_memory():
+    """With every library allocation routed through PyTorch's caching
+    allocator, repeated calls leave its counters unchanged (the dsg_bahmani
+    path, run the same way, does allocate: the check can see allocations)."""
+    stream = torch.cuda.current_stream()
+    c = oracle.from_raw(inputs.rmat(scale=14, m=1 << 18, seed=9))
+    off, adj = _device_csr(c)
+    mask = torch.empty(c.n, dtype=torch.uint8, device="cuda")
+    E, V = ctypes.c_uint64(), ctypes.c_uint64()
+    L = dsg.lib()
+
+    def call():
+        st = L.dsg_bahmani_noalloc(c.n, off.data_ptr(), adj.data_ptr(), 1, 10, mask.data_ptr(), ctypes.byref(E),
+                                   ctypes.byref(V), stream.cuda_stream)
+        assert st == N.DSG_OK, L.dsg_last_error()
+
+    dsg.use_torch_allocator(True)
+    try:
+        call()  # the first call in this context looks up the buffer's address
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == before
+        want = oracle.bahmani(c, 1, 10)
+        assert (E.value, V.value) == (want.E, want.V)
+        np.testing.assert_array_equal(mask.cpu().numpy(), want.mask)
+        g = dsg.Graph.from_csr(c.n, c.off, c.adj)
+        g.bahmani(1, 10)
+        g.close()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) > before
+    finally:
+        dsg.use_torch_allocator(False)
+
+
 def test_noalloc_rejects_graphs_beyond_the_fixed_buffer():
     n = 5_000_000  # eps = 0 needs a 16(n+2)-byte round history alone: above 64 MiB
     off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
