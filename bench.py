@@ -800,10 +800,26 @@ def workload_size(workload: str):
     return raw.n, raw.m_raw
 
 
+def replica_launch_cmd(argv, gpus: int, port: int):
+    """The command that runs this script as `gpus` replica ranks on one node
+    (torch.distributed.run, rendezvous on 127.0.0.1), forwarding argv."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+
+
 def main():
     args = parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # asked for N GPUs but started as one process: start the N replica ranks
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        return subprocess.call(replica_launch_cmd(sys.argv[1:], args.gpus, port))
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus and world > 1:
+        print(f"bench: --gpus {args.gpus} but {world} ranks were started; the ranks decide", file=sys.stderr)
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         if rank != 0:

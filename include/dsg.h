@@ -181,6 +181,49 @@ uint64_t dsg_round_bound(uint32_t n, uint32_t eps_num, uint32_t eps_den);
 dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const uint32_t* adj, uint32_t eps_num,
                                uint32_t eps_den, uint8_t* out_set, uint64_t* out_E, uint64_t* out_V, void* stream);
 
+/*
+ * Snapshot / resume of Algorithm 1 (Sec. 3.1).  The algorithm's state
+ * between two rounds -- each vertex's degree inside S_r or the round it
+ * failed in, the round r, |S_r|, |E(S_r)|, the densest round so far with its
+ * (|E|, |V|), and the per-round history -- is all it needs to go on, so a
+ * peel can be paused, written to host memory and continued later (on the
+ * same or another handle of the same graph, on any device) with exactly the
+ * result of an uninterrupted dsg_bahmani.
+ *   dsg_peel_begin         a paused peel of g at eps_num / eps_den, at round 0.
+ *                          g must outlive the state.
+ *   dsg_peel_advance       run at most max_rounds more rounds (0: to the end);
+ *                          *rounds (nullable) = rounds done so far, *done
+ *                          (nullable) = 1 once S is empty.
+ *   dsg_peel_snapshot_size bytes of its snapshot now: 8 (16 + 2 (r + 1)) +
+ *                          4 n.
+ *   dsg_peel_snapshot      write the snapshot into a caller-owned host buffer
+ *                          of at least that many bytes (DSG_EINVAL if smaller):
+ *                          16 u64 header words (magic "DSGPEEL1", version 1, n,
+ *                          m, p, q, r, |S_r|, |E(S_r)|, best round, best E,
+ *                          best V, history length r + 1, 3 reserved), the
+ *                          histories of |S_t| and |E(S_t)| (u64 each), then n
+ *                          u32 state words (degree, or 0x80000000 | failure
+ *                          round).
+ *   dsg_peel_resume        a paused peel rebuilt from a snapshot on g; DSG_EINVAL
+ *                          if the buffer is not a snapshot, is truncated, or was
+ *                          taken on a graph with another n or m.
+ *   dsg_peel_finish        run to the end; out_set (n bytes, host or device,
+ *                          nullable), out_E / out_V / out_rounds (nullable), and
+ *                          the histories into hist_S / hist_E (nullable, hist_cap
+ *                          slots; DSG_EOVERFLOW if fewer than R + 1, the scalars
+ *                          still written).  The state stays valid.
+ *   dsg_peel_free          release the state's device memory.
+ */
+typedef struct dsg_peel_state dsg_peel_state;
+dsg_status dsg_peel_begin(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, dsg_peel_state** out);
+dsg_status dsg_peel_advance(dsg_peel_state* st, uint32_t max_rounds, uint64_t* rounds, uint32_t* done);
+dsg_status dsg_peel_snapshot_size(const dsg_peel_state* st, uint64_t* bytes);
+dsg_status dsg_peel_snapshot(const dsg_peel_state* st, void* buf, uint64_t bytes);
+dsg_status dsg_peel_resume(const dsg_graph* g, const void* buf, uint64_t bytes, dsg_peel_state** out);
+dsg_status dsg_peel_finish(dsg_peel_state* st, uint8_t* out_set, uint64_t* out_E, uint64_t* out_V,
+                           uint64_t* out_rounds, uint64_t* hist_S, uint64_t* hist_E, uint64_t hist_cap);
+void dsg_peel_free(dsg_peel_state* st);
+
 /* --------------------------------------------- Algorithm 2, first phase */
 
 /*
@@ -237,6 +280,12 @@ typedef struct {
  * alone.  DSG_EINVAL on malformed offsets or eps_den == 0.
  */
 dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, void* stream);
+/* Which graphs of a batch the grid-wide kernels solve (before the
+ * block-per-graph launch): those whose work 2m + n exceeds min_work; 0 (the
+ * default) means those above twice one block's share of the batch's work and
+ * above 2^20; 0xffffffff keeps every graph in the block-per-graph launch.
+ * DSG_BATCH_SPLIT.  Results never depend on it. */
+dsg_status dsg_set_batch_split(uint32_t min_work);
 
 /* ------------------------------------------------------------- serving */
 
@@ -334,6 +383,13 @@ dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work);
  * level-wide queue in pieces of at most chunk_len entries, which every block
  * takes from.  Default 4096; DSG_INLINE_MAX.  Results never depend on it. */
 dsg_status dsg_set_inline_max(uint32_t inline_max);
+/* Core numbers: once at most max_vertices vertices remain after a level, the
+ * remaining graph is compacted (rows cut to the remaining neighbours, which
+ * leaves every remaining degree as it is) and one thread-block cluster runs
+ * the remaining levels with the degrees in its distributed shared memory.
+ * 0 turns it off; at most 131072 (16 blocks of 8192 vertices).  Default
+ * 65536; DSG_KCORE_TAIL.  Results never depend on it. */
+dsg_status dsg_set_kcore_tail(uint32_t max_vertices);
 
 /*
  * Densest k-core and CBDS-P (Algorithm 2).
@@ -395,8 +451,8 @@ void dsg_tune_clear(void);
 uint32_t dsg_tune_entries(void);
 /* The launch parameters a solve of kernel 0 (peel) or 1 (core numbers) on g
  * would use now: out = {block, blocks_per_sm, short_max, chunk_len, hot_deg,
- * local_max, local_work, inline_max}. */
-dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[8]);
+ * local_max, local_work, inline_max, kcore_tail}. */
+dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[9]);
 
 /*
  * Device-memory allocator hook (no counterpart in the paper; lets a host

@@ -160,17 +160,22 @@ def chung_lu_weights(n: int, gamma: float, mean: float, wmax: float) -> np.ndarr
     return w[:n]
 
 
+def batch_n(i: int, seed_base: int = 1000, n_lo: int = 1_000, n_hi: int = 1_000_000) -> int:
+    """Vertex count of batch member i (log-uniform in [n_lo, n_hi]), without generating it."""
+    lib = _load()
+    u = (lib.gen_draw(seed_base + i, 7, 0) >> 11) * 2.0 ** -53
+    n = int(math.floor(math.exp(math.log(n_lo) + u * (math.log(n_hi) - math.log(n_lo)))))
+    return max(n_lo, min(n_hi, n))
+
+
 def batch_graph(i: int, seed_base: int = 1000, n_lo: int = 1_000, n_hi: int = 1_000_000,
                 threads: int | None = None) -> RawGraph:
     """Member i of the uneven batch: n log-uniform in [n_lo, n_hi]; even i is
     Erdos-Renyi with mean degree 8 (4n uniform pairs), odd i is Chung-Lu
     (exponent 2.3, mean degree 16, structural cut-off sqrt(16 n)); each gets a
     planted block of floor(sqrt(n)) vertices at edge probability 0.3."""
-    lib = _load()
     seed = seed_base + i
-    u = (lib.gen_draw(seed, 7, 0) >> 11) * 2.0 ** -53
-    n = int(math.floor(math.exp(math.log(n_lo) + u * (math.log(n_hi) - math.log(n_lo)))))
-    n = max(n_lo, min(n_hi, n))
+    n = batch_n(i, seed_base, n_lo, n_hi)
     k = int(math.isqrt(n))
     if i % 2 == 0:
         base = er_pairs(n, 4 * n, seed, threads)

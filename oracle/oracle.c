@@ -356,7 +356,10 @@ int orc_kcore_pkc(uint32_t n, const uint64_t* off, const uint32_t* adj, uint32_t
  * Tatti et al.).  For every k with a non-empty k-core: V_k = #{v : core >= k},
  * E_k = #{edges whose endpoints both have core >= k}; the best k is the one
  * of largest E_k / V_k, the smallest such k on ties (levels are visited in
- * increasing k with a strict comparison).
+ * increasing k with a strict comparison).  Algorithm 2 takes a level's
+ * density after that level's vertices joined `visited` yet labels it with k;
+ * the label is paired here with the k-core {core >= k} itself, the set its
+ * second phase compares neighbours against (deg >= max_density_core).
  * out[0] = k*, out[1] = E_k*, out[2] = V_k*.  n == 0 gives zeros.
  */
 int orc_densest_core(uint32_t n, const uint64_t* off, const uint32_t* adj, const uint32_t* core, uint64_t* out) {

@@ -23,7 +23,7 @@ from . import _native as N
 from ._native import (DSG_CSR_CANONICALIZE, DSG_CSR_VALIDATE, DSG_PTRS_DEVICE, DsgError,  # noqa: F401
                       lib)
 
-__all__ = ["Graph", "Trace", "BatchSolver", "pack_batch", "Server", "DsgError", "lib", "round_bound", "set_tuning", "get_tuning", "set_wait_limit_ns",
+__all__ = ["Graph", "Trace", "PeelState", "BatchSolver", "pack_batch", "Server", "DsgError", "lib", "round_bound", "set_tuning", "get_tuning", "set_wait_limit_ns",
            "DSG_CSR_CANONICALIZE", "DSG_CSR_VALIDATE", "DSG_PTRS_DEVICE"]
 
 
@@ -32,11 +32,14 @@ def round_bound(n: int, p: int, q: int) -> int:
 
 
 def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, chunk_len: int = 256,
-               hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384, inline_max: int = 4096):
+               hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384, inline_max: int = 4096,
+               kcore_tail: int = 65536, batch_split: int = 0):
     N.check(lib().dsg_set_tuning(block, blocks_per_sm, short_max, chunk_len), "set_tuning")
     N.check(lib().dsg_set_hot_degree(hot_deg), "set_hot_degree")
     N.check(lib().dsg_set_local_max(local_max, local_work), "set_local_max")
     N.check(lib().dsg_set_inline_max(inline_max), "set_inline_max")
+    N.check(lib().dsg_set_kcore_tail(kcore_tail), "set_kcore_tail")
+    N.check(lib().dsg_set_batch_split(batch_split), "set_batch_split")
 
 
 def get_tuning():
@@ -303,10 +306,10 @@ class Graph:
 
     def tuning(self, kernel: str = "peel") -> dict:
         """Launch parameters a solve of `kernel` ("peel" or "kcore") on this graph uses now."""
-        v = (ctypes.c_uint32 * 8)()
+        v = (ctypes.c_uint32 * 9)()
         N.check(lib().dsg_tune_lookup(self._h, 0 if kernel == "peel" else 1, v), "tune_lookup")
         return dict(zip(("block", "blocks_per_sm", "short_max", "chunk_len", "hot_deg", "local_max", "local_work",
-                         "inline_max"), list(v)))
+                         "inline_max", "kcore_tail"), list(v)))
 
     def kcore(self, out=None):
         """Core numbers (Algorithm 2, first phase)."""
@@ -328,6 +331,70 @@ class Graph:
             out = out[:self.n]
         keys = ("levels", "pieces", "rem_scanned", "rem_written", "atomics")
         return out, {k: int(v) for k, v in zip(keys, st)}
+
+
+class PeelState:
+    """A paused Algorithm 1 peel (dsg_peel_*): advance it some rounds, write a
+    snapshot (bytes), resume it from one on a handle of the same graph, or
+    finish it.  Finishing gives exactly dsg_bahmani's result."""
+
+    def __init__(self, handle, graph, p: int, q: int):
+        self._h = handle
+        self._graph = graph  # the graph must outlive the state
+        self.p, self.q = p, q
+
+    @classmethod
+    def begin(cls, graph: "Graph", p: int, q: int) -> "PeelState":
+        h = ctypes.c_void_p()
+        N.check(lib().dsg_peel_begin(graph._h, p, q, ctypes.byref(h)), "peel_begin")
+        return cls(h, graph, p, q)
+
+    @classmethod
+    def resume(cls, graph: "Graph", snap: bytes) -> "PeelState":
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(bytes(snap), len(snap))
+        N.check(lib().dsg_peel_resume(graph._h, buf, len(snap), ctypes.byref(h)), "peel_resume")
+        hdr = np.frombuffer(bytes(snap)[:128], np.uint64)
+        return cls(h, graph, int(hdr[4]), int(hdr[5]))
+
+    def advance(self, max_rounds: int = 0):
+        """Run at most max_rounds more rounds (0: to the end); returns (rounds so far, done)."""
+        r = ctypes.c_uint64()
+        d = ctypes.c_uint32()
+        N.check(lib().dsg_peel_advance(self._h, int(max_rounds), ctypes.byref(r), ctypes.byref(d)), "peel_advance")
+        return int(r.value), bool(d.value)
+
+    def snapshot(self) -> bytes:
+        size = ctypes.c_uint64()
+        N.check(lib().dsg_peel_snapshot_size(self._h, ctypes.byref(size)), "peel_snapshot_size")
+        buf = ctypes.create_string_buffer(int(size.value))
+        N.check(lib().dsg_peel_snapshot(self._h, buf, size.value), "peel_snapshot")
+        return buf.raw
+
+    def finish(self, out_set=None, want_set: bool = True) -> Trace:
+        n = self._graph.n
+        if out_set is None and want_set:
+            out_set = np.zeros(max(n, 1), np.uint8)
+        cap = round_bound(n, self.p, self.q) + 1
+        hs = np.zeros(cap, np.uint64)
+        he = np.zeros(cap, np.uint64)
+        E, V, R = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        N.check(lib().dsg_peel_finish(self._h, N.ptr(out_set), ctypes.byref(E), ctypes.byref(V), ctypes.byref(R),
+                                      N.ptr(hs), N.ptr(he), cap), "peel_finish")
+        k = int(R.value) + 1
+        mask = out_set[:n] if isinstance(out_set, np.ndarray) else out_set
+        return Trace(int(R.value), -1, int(E.value), int(V.value), hs[:k], he[:k], None, mask, 2 * self._graph.m, 0)
+
+    def close(self):
+        if self._h:
+            lib().dsg_peel_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ batches

@@ -94,6 +94,13 @@ _SIGS = [
     ("dsg_bahmani_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, c.POINTER(Trace)]),
     ("dsg_round_bound", c.c_uint64, [c.c_uint32, c.c_uint32, c.c_uint32]),
     ("dsg_bahmani_noalloc", c.c_int, [c.c_uint32, _VP, _VP, c.c_uint32, c.c_uint32, _VP, _U64P, _U64P, _VP]),
+    ("dsg_peel_begin", c.c_int, [_VP, c.c_uint32, c.c_uint32, c.POINTER(_VP)]),
+    ("dsg_peel_advance", c.c_int, [_VP, c.c_uint32, _U64P, _U32P]),
+    ("dsg_peel_snapshot_size", c.c_int, [_VP, _U64P]),
+    ("dsg_peel_snapshot", c.c_int, [_VP, _VP, c.c_uint64]),
+    ("dsg_peel_resume", c.c_int, [_VP, _VP, c.c_uint64, c.POINTER(_VP)]),
+    ("dsg_peel_finish", c.c_int, [_VP, _VP, _U64P, _U64P, _U64P, _VP, _VP, c.c_uint64]),
+    ("dsg_peel_free", None, [_VP]),
     ("dsg_kcore", c.c_int, [_VP, _VP]),
     ("dsg_densest_core", c.c_int, [_VP, _VP, _VP, _VP, c.POINTER(CbdsResult)]),
     ("dsg_cbds", c.c_int, [_VP, _VP, _VP, _VP, c.POINTER(CbdsResult)]),
@@ -119,6 +126,8 @@ _SIGS = [
     ("dsg_graph_view", c.c_int, [_VP, _VP, c.POINTER(_VP)]),
     ("dsg_solve", c.c_int, [_VP, c.c_uint32, _U32P, _U32P, c.POINTER(_VP), _U64P, _U64P, _VP]),
     ("dsg_set_inline_max", c.c_int, [c.c_uint32]),
+    ("dsg_set_kcore_tail", c.c_int, [c.c_uint32]),
+    ("dsg_set_batch_split", c.c_int, [c.c_uint32]),
     ("dsg_set_allocator", None, [ALLOC_FN, FREE_FN, _VP]),
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),
     ("dsg_debug_peel_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, _U64P, c.c_uint64, _U64P]),

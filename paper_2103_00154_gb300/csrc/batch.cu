@@ -384,7 +384,10 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
     for (uint32_t g = 0; g < G; ++g) total_work += work(g);
     const uint64_t share = total_work / slots;
     uint32_t nbig = 0;
-    while (nbig < G && work(order[nbig]) > 2 * share && work(order[nbig]) > (1u << 20)) ++nbig;
+    if (tu.batch_split)
+        while (nbig < G && work(order[nbig]) > tu.batch_split) ++nbig;
+    else
+        while (nbig < G && work(order[nbig]) > 2 * share && work(order[nbig]) > (1u << 20)) ++nbig;
     std::vector<uint64_t> res(4 * (size_t)G, 0);
     for (uint32_t i = 0; i < nbig; ++i) {
         const uint32_t g = order[i];

@@ -9,7 +9,10 @@
 //   hE[c] = #{edges {u, v} : min(core(u), core(v)) = c}
 // so that V_k and E_k are suffix sums of hV and hE, and the smallest k of
 // highest density wins (strict comparison with increasing k, Algorithm 2's
-// maximum update).
+// maximum update).  Label k goes with the k-core {core >= k} (Algorithm 2
+// measures a level's density once its vertices joined `visited`, but its
+// second phase compares against the labelled core, so label and set are
+// taken to be the same core).
 //
 // Phase 2 of Algorithm 2 then grows the densest core by vertices outside it:
 //   eligible v: core(v) lies strictly between the core's density E_k/V_k and k*

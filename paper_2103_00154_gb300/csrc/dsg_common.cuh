@@ -102,6 +102,7 @@ struct dsg_graph {
     cudaStream_t stream = nullptr;
     uint32_t max_blocks = 0; // cap on the grid of persistent kernels for this handle (0: whole GPU)
     uint32_t force_block = 0; // block size of those kernels regardless of tuning (0: tuned)
+    bool no_tail = false;     // core numbers: keep every level in the grid-wide kernel
 };
 
 // -------------------------------------------------------------- device side

@@ -27,6 +27,10 @@ struct Tuning {
     uint32_t local_work = 16384; // k-core: ... while that block's local share of the sub-round stays within this
     uint32_t inline_max = 4096;  // k-core: rows up to this length claimed by a block's level scan are drained by
                                  // that block; longer ones by every warp in the next sub-round
+    uint32_t tail_max = 65536;   // k-core: once at most this many vertices remain, one thread-block cluster
+                                 // finishes the levels on the compacted remaining graph (0: never)
+    uint32_t batch_split = 0;    // batches: a graph whose work (2m + n) exceeds this is solved by the
+                                 // grid-wide kernels (0: above twice a block's share and 2^20)
 };
 
 Tuning current_tuning();
@@ -66,6 +70,16 @@ dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_de
 // Core numbers of a graph into core_out (host or device); stats nullable.
 dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
                      uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0, uint64_t* stamps = nullptr);
+
+// The last levels of the core numbers on the compacted remaining graph (the
+// vertices whose claim bit is clear; deg holds their degrees), by one
+// thread-block cluster; writes their core numbers into deg and adds its
+// levels, scanned remaining entries and atomics into stats5[0], [2], [4];
+// with a trace buffer, block 0 stamps each level's phases there.
+constexpr uint32_t kTailMaxVertices = 16 * 8192;
+dsg_status kcore_tail(uint32_t n, const uint64_t* off, const uint32_t* adj, uint32_t* deg, const uint32_t* claim,
+                      uint32_t cap, cudaStream_t s, uint64_t* stats5, uint64_t* trace = nullptr,
+                      uint64_t trace_cap = 0, uint64_t* stamps = nullptr);
 
 // Device check that a graph is canonical (sorted rows, no loops, no repeats,
 // symmetric, ids < n).  DSG_EINVAL with a message if not.

@@ -1,22 +1,22 @@
 // CSR ingest: raw undirected pairs -> canonical CSR (Def. 1: a simple graph,
 // E a set of edges between distinct vertices).
 //
-//   1. count   every non-loop pair adds one to the row of each endpoint
-//              (frequent endpoints, found from a sample of the pairs, are
-//              counted per block in shared memory)
-//   2. scan    row starts of the (still repeated) entries
-//   3. scatter each pair is written into both rows (a frequent endpoint's
-//              entries from one block go to a range reserved for that block)
-//   4. sort    each row sorted and de-duplicated in place; rows are binned by
-//              length: <= 32 entries one warp, one value per lane; <= 1024
-//              one warp holding up to 32 values per lane (register bitonic
-//              network, no shared memory); <= 8192 one block (each warp sorts
-//              1024 values in registers, cross-warp merge steps go through
-//              shared memory); longer ("giant") rows are split by value
-//              window and each window is de-duplicated and ordered through a
-//              shared-memory bitmap
-//   5. scan    final row lengths -> off
-//   6. copy    unique entries into adj
+//   1. histogram  the non-loop entries (each pair gives owner -> neighbour in
+//                 both directions) counted over <= 2^16 ranges of vertex ids
+//   2. plan       ranges cut into buckets of consecutive owners holding
+//                 similar numbers of entries
+//   3. scatter    every entry appended to its owner's bucket
+//   4. rows       one block per bucket: its owners' counts, row starts and
+//                 entries placed in their rows, in shared memory
+//   5. sort       each row sorted and de-duplicated in place; rows are binned
+//                 by length: <= 32 entries one warp, one value per lane;
+//                 <= 1024 one warp holding up to 32 values per lane (register
+//                 bitonic network, no shared memory); <= 8192 one block (each
+//                 warp sorts 1024 values in registers, cross-warp merge steps
+//                 go through shared memory); longer ("giant") rows one block
+//                 each, by a stable LSD radix sort on 8-bit digits
+//   6. scan       final row lengths -> off
+//   7. copy       unique entries into adj
 // The result is byte-identical to sorting the (min, max) keys and removing
 // repeats, because a canonical CSR of a given edge set is unique.
 #include <cooperative_groups.h>
@@ -33,9 +33,6 @@ namespace dsg {
 constexpr uint32_t kPad = 0xffffffffu;
 constexpr uint32_t kScanTile = 2048;
 constexpr uint32_t kBlockRowMax = 8192;  // longest row sorted by one block (8 warps x 1024)
-constexpr uint32_t kWinBits = 13;        // giant rows: value windows of 8192 ids
-constexpr uint32_t kWin = 1u << kWinBits;
-constexpr uint32_t kWinWords = kWin / 32;
 constexpr int kClasses = 9;              // 0..4: warp rows E = 2..32, 5..7: block rows of 2/4/8 warps, 8: giant
 constexpr int kGiant = 8;
 
@@ -123,271 +120,562 @@ static cudaError_t device_scan(const uint32_t* in, uint64_t n, uint64_t* out, ui
     return cudaGetLastError();
 }
 
+// Exclusive scan of n uint32 values into out[0..n], out[n] = total (device
+// buffers, stream-ordered; the tile sums live in sc).
+dsg_status scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, Scratch& sc, cudaStream_t s) {
+    uint64_t* sums;
+    DSG_TRY_CUDA(sc.get(&sums, n / kScanTile + 2));
+    DSG_TRY_CUDA(device_scan(in, n, out, sums, s));
+    return DSG_OK;
+}
+
 // ----------------------------------------------------------- count / scatter
 
-// ------------------------------------------------ hot vertices (count, scatter)
-// A vertex that is an endpoint of a large share of the raw pairs (a hub)
-// would take one global atomic per pair in count and scatter, all on one
-// address.  A sample of the pairs names such vertices; count and scatter
-// then combine their increments per block in shared memory, and each block
-// writes a hub's entries into a range of the hub's row reserved for it (the
-// blocks' counts are prefix-summed per hub between the two passes).  Which
-// vertices are hot only changes speed, never the result.
-constexpr uint32_t kHotMax = 1024;          // hot vertices at most
-constexpr uint32_t kHotSlots = 2048;        // shared-memory hash of the hot ids
-constexpr uint32_t kSamplePairs = 32768;    // pairs sampled to find them
-constexpr uint32_t kSampleSlots = 8192;     // shared-memory hash of the sampled endpoints
-constexpr uint32_t kHotMinHits = 4;         // sample hits that make a vertex hot
-constexpr uint32_t kHotEmpty = 0xffffffffu;
-constexpr uint64_t kHotPassMinPairs = 1ull << 22;  // inputs with fewer pairs skip the pass
+// ------------------------------------------ bucketed count and scatter
+// Rows are built without a global atomic per entry.  The directed entries
+// (owner -> neighbour; each non-loop pair gives two) are first appended to
+// buckets of consecutive owners -- one global atomic per block tile and
+// bucket, and each bucket's tail is written sequentially, so the writes merge
+// into whole sectors in L2 -- and then one block per bucket counts the
+// bucket's owners and places their entries with shared-memory counters and
+// cursors, writing only inside the bucket's own (small) region of the rows.
+// Bucket boundaries come from an exact histogram of the entries over at most
+// 2^15 equal ranges of vertex ids: a range starts a new bucket where the
+// entries before it cross a multiple of the target bucket size, or every
+// span_cut ranges (so a bucket's vertices fit the row builder's counters),
+// so buckets hold similar numbers of entries whatever the degree
+// distribution.  Which buckets are formed changes speed, never the result.
+constexpr uint32_t kRangesMax = 32768;
+constexpr uint32_t kBucketTarget = 8192;     // buckets aimed for by entry count
+constexpr uint64_t kBucketMinEntries = 4096; // ... but none smaller than this by entry count
+constexpr uint32_t kSpanMax = 16384;         // owners the row builder counts at once (64 KB of counters)
+constexpr uint32_t kSpanCutBuckets = 4096;   // span cuts at most
+constexpr uint32_t kBucketsMax = kBucketTarget + 1 + kSpanCutBuckets + 1;
 
-__device__ __forceinline__ uint32_t hot_hash(uint32_t x) { return (x * 0x9E3779B1u) >> 21; }  // 11 bits
-
-__host__ __device__ __forceinline__ uint64_t sample_stride(uint64_t m_raw) {
-    return m_raw > kSamplePairs ? m_raw / kSamplePairs : 1;
-}
-__host__ __device__ __forceinline__ uint64_t sample_take(uint64_t m_raw) {
-    return m_raw < kSamplePairs ? m_raw : kSamplePairs;
-}
-
-// Gather every stride-th pair into one contiguous buffer, a pair per thread
-// over many SMs (one block fetching 32 K scattered pairs is bound by its own
-// outstanding loads).
-__global__ void __launch_bounds__(256) hot_gather(uint64_t m_raw, const uint32_t* __restrict__ src,
-                                                  const uint32_t* __restrict__ dst, uint2* __restrict__ sample) {
-    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < sample_take(m_raw)) {
-        const uint64_t at = k * sample_stride(m_raw);
-        sample[k] = make_uint2(src[at], dst[at]);
-    }
-}
-
-// Endpoint frequencies over the gathered sample, split over kHotParts blocks
-// by a hash of the id (every block reads the whole sample and counts only its
-// own part, so no id is counted twice and the hashing work is shared).  Each
-// block lists its ids with at least kHotMinHits hits as (id, hits capped at
-// 255) and adds them to a histogram of the hit counts.
-constexpr uint32_t kHotParts = 8;
-
-__device__ __forceinline__ uint32_t hot_part(uint32_t x) { return (x * 0x9E3779B1u) >> 29; }  // 3 bits
-__device__ __forceinline__ uint32_t sample_slot(uint32_t x) { return (x * 0x85EBCA6Bu) >> 19; }  // 13 bits
-
-__global__ void __launch_bounds__(1024) hot_sample(uint32_t n, uint64_t m_raw, const uint2* __restrict__ sample,
-                                                   uint2* __restrict__ cand, uint32_t* __restrict__ cand_n,
-                                                   uint32_t* __restrict__ hist) {
-    extern __shared__ uint32_t sample_smem[];  // kSampleSlots keys, then kSampleSlots counts
-    uint32_t* key = sample_smem;
-    uint32_t* cnt = sample_smem + kSampleSlots;
-    __shared__ uint32_t lhist[256];
-    __shared__ uint32_t nq, base, fill;
-    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x) {
-        key[i] = kHotEmpty;
-        cnt[i] = 0;
-    }
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) lhist[i] = 0;
-    if (threadIdx.x == 0) nq = fill = 0;
-    __syncthreads();
-    const uint64_t take = sample_take(m_raw);
-    constexpr uint32_t kU = 8;  // pairs loaded per thread before any is counted
-    for (uint64_t k0 = threadIdx.x; k0 < take; k0 += (uint64_t)blockDim.x * kU) {
-        uint32_t e[2 * kU];
-#pragma unroll
-        for (uint32_t t = 0; t < kU; ++t) {
-            const uint64_t k = k0 + (uint64_t)t * blockDim.x;
-            e[2 * t] = e[2 * t + 1] = kHotEmpty;
-            if (k < take) {
-                const uint2 p = sample[k];
-                e[2 * t] = p.x;
-                e[2 * t + 1] = p.y;
-            }
-        }
-#pragma unroll
-        for (uint32_t t = 0; t < 2 * kU; ++t) {
-            const uint32_t x = e[t];
-            if (x >= n || e[t ^ 1u] == x || hot_part(x) != blockIdx.x) continue;  // padding, a loop, another part
-            uint32_t h = sample_slot(x);
-            for (uint32_t probe = 0; probe < 8; ++probe, h = (h + 1) & (kSampleSlots - 1)) {
-                const uint32_t cur = key[h];
-                const uint32_t prev = cur == x ? x : (cur == kHotEmpty ? atomicCAS(&key[h], kHotEmpty, x) : cur);
-                if (prev == kHotEmpty || prev == x) {
-                    atomicAdd(&cnt[h], 1u);
-                    break;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x)
-        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) {
-            atomicAdd(&lhist[min(cnt[i], 255u)], 1u);
-            atomicAdd(&nq, 1u);
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) base = nq ? atomicAdd(cand_n, nq) : 0u;
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x)
-        if (lhist[i]) atomicAdd(&hist[i], lhist[i]);
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kSampleSlots; i += blockDim.x)
-        if (key[i] != kHotEmpty && cnt[i] >= kHotMinHits) cand[base + atomicAdd(&fill, 1u)] = make_uint2(key[i], min(cnt[i], 255u));
-}
-
-// Keep the most frequent candidates: the histogram of their hit counts gives
-// the count above which all fit in kHotMax, and the boundary count fills the rest.
-__global__ void __launch_bounds__(1024) hot_select(const uint2* __restrict__ cand, const uint32_t* __restrict__ cand_n,
-                                                   const uint32_t* __restrict__ hist, uint32_t* __restrict__ hot_ids,
-                                                   uint32_t* __restrict__ hot_n) {
-    __shared__ uint32_t cut, room, extra, nsel;
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0, b = 255;
-        while (b >= kHotMinHits && acc + hist[b] <= kHotMax) acc += hist[b--];
-        cut = b;                // buckets above cut are taken whole
-        room = kHotMax - acc;  // slots left for bucket cut
-        extra = 0;
-        nsel = 0;
-    }
-    __syncthreads();
-    const uint32_t nc = *cand_n;
-    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
-        const uint2 c = cand[i];
-        bool take = c.y > cut;
-        if (!take && c.y == cut) take = atomicAdd(&extra, 1u) < room;
-        if (take) {
-            const uint32_t at = atomicAdd(&nsel, 1u);
-            if (at < kHotMax) hot_ids[at] = c.x;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *hot_n = min(nsel, kHotMax);
-}
-
-// Shared-memory table of the hot ids: slot -> (id, index in the hot list).
-struct HotTable {
-    uint32_t key[kHotSlots];
-    uint16_t idx[kHotSlots];
-    uint32_t local[kHotMax];  // this block's count or cursor per hot vertex
+struct BucketPlan {
+    uint32_t rshift;    // range of a vertex v: v >> rshift
+    uint32_t nranges;   // ceil(n / 2^rshift) <= kRangesMax
+    uint32_t span_cut;  // a bucket also starts at every multiple of span_cut ranges
 };
 
-__device__ __forceinline__ void hot_build(HotTable& t, const uint32_t* hot_ids, uint32_t hot_n) {
-    for (uint32_t i = threadIdx.x; i < kHotSlots; i += blockDim.x) t.key[i] = kHotEmpty;
-    for (uint32_t i = threadIdx.x; i < kHotMax; i += blockDim.x) t.local[i] = 0;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < hot_n; i += blockDim.x) {
-        const uint32_t x = hot_ids[i];
-        uint32_t h = hot_hash(x);
-        while (true) {
-            if (atomicCAS(&t.key[h], kHotEmpty, x) == kHotEmpty) {
-                t.idx[h] = (uint16_t)i;
-                break;
-            }
-            h = (h + 1) & (kHotSlots - 1);
-        }
-    }
-    __syncthreads();
+static BucketPlan bucket_plan_for(uint32_t n) {
+    BucketPlan pl;
+    pl.rshift = 0;
+    while (((uint64_t)n + (1ull << pl.rshift) - 1) >> pl.rshift > kRangesMax) ++pl.rshift;
+    pl.nranges = (uint32_t)(((uint64_t)n + (1ull << pl.rshift) - 1) >> pl.rshift);
+    const uint32_t width = 1u << pl.rshift;
+    uint32_t cut = width <= kSpanMax ? kSpanMax / width : 1;
+    const uint32_t need = (pl.nranges + kSpanCutBuckets - 1) / kSpanCutBuckets;  // at most kSpanCutBuckets cuts
+    pl.span_cut = cut > need ? cut : need;
+    return pl;
 }
 
-// index of x in the hot list, or -1
-__device__ __forceinline__ int hot_find(const HotTable& t, uint32_t x) {
-    uint32_t h = hot_hash(x);
-    while (true) {
-        const uint32_t k = t.key[h];
-        if (k == x) return t.idx[h];
-        if (k == kHotEmpty) return -1;
-        h = (h + 1) & (kHotSlots - 1);
-    }
-}
-
-// count: one per endpoint of every non-loop pair; hot endpoints are counted
-// in shared memory and also recorded per block (blk[block * kHotMax + h]).
-__global__ void __launch_bounds__(256) count_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
-                                                    const uint32_t* __restrict__ dst, uint32_t* __restrict__ cnt,
-                                                    const uint32_t* __restrict__ hot_ids,
-                                                    const uint32_t* __restrict__ hot_n_p, uint32_t* __restrict__ blk,
-                                                    IngestCtl* ctl) {
-    __shared__ HotTable t;
-    const uint32_t hot_n = *hot_n_p;
-    hot_build(t, hot_ids, hot_n);
+// Exact histogram of the entries over the vertex ranges: each block counts
+// its share of the pairs in shared memory (32-bit counts) and adds its counts
+// to the global ones once.  Ids out of range set ERR_RANGE.
+__global__ void __launch_bounds__(1024) range_hist_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
+                                                          const uint32_t* __restrict__ dst, BucketPlan pl,
+                                                          uint32_t* __restrict__ range_cnt, IngestCtl* ctl) {
+    extern __shared__ uint32_t hc[];
+    for (uint32_t r = threadIdx.x; r < pl.nranges; r += blockDim.x) hc[r] = 0;
+    __syncthreads();
+    bool bad = false;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_raw;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t u = src[i], v = dst[i];
+        const uint32_t u = src[i], v = dst[i];
         if (u >= n || v >= n) {
-            atomicOr(&ctl->err, ERR_RANGE);
+            bad = true;
             continue;
         }
         if (u == v) continue;
-        int hu = hot_find(t, u), hv = hot_find(t, v);
-        if (hu >= 0) atomicAdd(&t.local[hu], 1u); else atomicAdd(&cnt[u], 1u);
-        if (hv >= 0) atomicAdd(&t.local[hv], 1u); else atomicAdd(&cnt[v], 1u);
+        atomicAdd(&hc[u >> pl.rshift], 1u);
+        atomicAdd(&hc[v >> pl.rshift], 1u);
     }
     __syncthreads();
-    for (uint32_t h = threadIdx.x; h < hot_n; h += blockDim.x) {
-        const uint32_t c = t.local[h];
-        blk[(uint64_t)blockIdx.x * kHotMax + h] = c;
-        if (c) atomicAdd(&cnt[hot_ids[h]], c);
-    }
+    for (uint32_t r = threadIdx.x; r < pl.nranges; r += blockDim.x)
+        if (hc[r]) atomicAdd(&range_cnt[r], hc[r]);
+    if (bad) atomicOr(&ctl->err, ERR_RANGE);
 }
 
-// per hot vertex h: exclusive prefix of the blocks' counts -> each block's
-// first slot in the hub's row
-__global__ void __launch_bounds__(256) hot_block_bases(const uint32_t* __restrict__ hot_n_p, uint32_t nblk,
-                                                       uint32_t* __restrict__ blk) {
+// One block: buckets from the range histogram.  Range r starts a bucket when
+// r == 0, when the entries before it and those before range r-1 lie in
+// different multiples of the target, or when r is a multiple of span_cut.
+// Writes range_bucket[r], the first vertex and the entry base of every
+// bucket (bucket_v0[F] = n, bucket_base[F] = total entries), start[n] =
+// total, *nb = F and *maxb = the largest bucket's entries.
+constexpr uint32_t kPlanPer = kRangesMax / 1024;  // ranges per thread
+
+__global__ void __launch_bounds__(1024) bucket_plan_kernel(uint32_t n, const uint32_t* __restrict__ range_cnt,
+                                                           BucketPlan pl, uint16_t* __restrict__ range_bucket,
+                                                           uint32_t* __restrict__ bucket_v0,
+                                                           uint64_t* __restrict__ bucket_base,
+                                                           uint64_t* __restrict__ start, uint32_t* __restrict__ nb,
+                                                           unsigned long long* __restrict__ maxb) {
+    __shared__ uint64_t tmp64[33];
+    __shared__ uint32_t tmp32[33];
+    const uint32_t r0 = threadIdx.x * kPlanPer;
+    auto c = [&](uint32_t j) -> uint64_t { return r0 + j < pl.nranges ? range_cnt[r0 + j] : 0; };
+    uint64_t mine = 0;
+    for (uint32_t j = 0; j < kPlanPer; ++j) mine += c(j);
+    uint64_t total;
+    uint64_t pre = block_excl_scan<uint64_t>(mine, tmp64, &total);
+    uint64_t target = (total + kBucketTarget - 1) / kBucketTarget;
+    if (target < kBucketMinEntries) target = kBucketMinEntries;
+    // flags, then bucket ids by a scan of the flags
+    uint64_t flags = 0;
+    uint32_t nf = 0;
+    uint64_t p = pre;  // entries before range r0 + j
+    for (uint32_t j = 0; j < kPlanPer; ++j) {
+        const uint32_t r = r0 + j;
+        const uint64_t cj = c(j);
+        if (r < pl.nranges) {
+            const uint64_t prev = r == 0 ? 0 : p - range_cnt[r - 1];
+            const bool f = r == 0 || p / target != prev / target || r % pl.span_cut == 0;
+            if (f) {
+                flags |= 1ull << j;
+                ++nf;
+            }
+        }
+        p += cj;
+    }
+    uint32_t nf_total;
+    const uint32_t id0 = block_excl_scan<uint32_t>(nf, tmp32, &nf_total);
+    uint32_t id = id0;
+    p = pre;
+    for (uint32_t j = 0; j < kPlanPer; ++j) {
+        const uint32_t r = r0 + j;
+        if (r < pl.nranges) {
+            if (flags >> j & 1ull) {
+                bucket_v0[id] = r << pl.rshift;
+                bucket_base[id] = p;
+                ++id;
+            }
+            range_bucket[r] = (uint16_t)(id - 1);
+        }
+        p += c(j);
+    }
+    if (threadIdx.x == 0) {
+        bucket_v0[nf_total] = n;
+        bucket_base[nf_total] = total;
+        start[n] = total;
+        *nb = nf_total;
+    }
+    __syncthreads();  // every bucket base is written (and visible to the block)
+    uint64_t big = 0;
+    for (uint32_t b = id0; b < id; ++b) big = max(big, bucket_base[b + 1] - bucket_base[b]);
+    if (big) atomicMax(maxb, (unsigned long long)big);
+}
+
+// The buckets are reached in two partition passes of small fan-out, so that a
+// block's tile holds many entries for each destination and writes them as
+// contiguous runs: pass A sends every entry of the raw pairs to its group of
+// kGroupFine consecutive buckets, pass B splits each group into its buckets.
+// A pass ranks a tile's entries per destination in shared memory, reserves
+// each destination's share with one global atomic, reorders the tile in
+// shared memory by destination and writes it out, consecutive threads to
+// consecutive addresses.  Entries are owner << 32 | neighbour.
+constexpr uint32_t kGroupFine = 64;                                       // buckets per group
+constexpr uint32_t kPartTB = 512;
+constexpr uint32_t kPartPer = 8;                                          // entries per thread and tile
+constexpr uint32_t kPartTile = kPartTB * kPartPer;                        // entries per tile
+constexpr uint32_t kBigChunk = 32768;  // entries per work item of a big bucket in the row builder
+constexpr uint32_t kRowsTB = 512;      // threads of the row builder's blocks
+
+// Per-bucket and per-group work: the groups' entry bases, pass B's chunks of
+// each group, the row builder's items (one per bucket, or one per kBigChunk
+// entries of a bucket above twice the target: a "big" bucket), as prefix
+// arrays the consumers search.  One block.
+struct PartPlan {
+    uint32_t groups;       // G
+    uint32_t b_items;      // pass B chunks in all
+    uint32_t r_items;      // row-builder items in all
+    uint32_t big;          // big buckets
+    uint64_t target;       // bucket target (entries)
+};
+
+__global__ void __launch_bounds__(1024) part_plan_kernel(const uint32_t* __restrict__ nbp,
+                                                         const uint64_t* __restrict__ bucket_base,
+                                                         uint64_t* __restrict__ group_base,
+                                                         uint32_t* __restrict__ b_pre, uint32_t* __restrict__ r_pre,
+                                                         uint32_t* __restrict__ big_list, PartPlan* __restrict__ pp) {
     __shared__ uint32_t tmp[33];
-    const uint32_t h = blockIdx.x;
-    if (h >= *hot_n_p) return;
-    uint32_t carry = 0;
-    for (uint32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
-        const uint32_t b = b0 + threadIdx.x;
-        const uint32_t c = b < nblk ? blk[(uint64_t)b * kHotMax + h] : 0u;
+    const uint32_t F = *nbp;
+    const uint64_t total = bucket_base[F];
+    uint64_t target = (total + kBucketTarget - 1) / kBucketTarget;
+    if (target < kBucketMinEntries) target = kBucketMinEntries;
+    const uint32_t G = (F + kGroupFine - 1) / kGroupFine;
+    // groups: base and pass-B chunk counts (G <= kGroupsMax <= 1024: one per thread)
+    {
+        const uint32_t g = threadIdx.x;
+        uint32_t chunks = 0;
+        if (g <= G) group_base[g] = bucket_base[min(g * kGroupFine, F)];
+        if (g < G) {
+            const uint64_t m = bucket_base[min((g + 1) * kGroupFine, F)] - bucket_base[g * kGroupFine];
+            chunks = (uint32_t)((m + kPartTile - 1) / kPartTile);
+        }
         uint32_t tot;
-        const uint32_t pre = block_excl_scan<uint32_t>(c, tmp, &tot);
-        if (b < nblk) blk[(uint64_t)b * kHotMax + h] = carry + pre;
+        const uint32_t pre = block_excl_scan<uint32_t>(chunks, tmp, &tot);
+        if (g < G) b_pre[g] = pre;
+        if (threadIdx.x == 0) {
+            b_pre[G] = tot;
+            pp->b_items = tot;
+            pp->groups = G;
+            pp->target = target;
+        }
+    }
+    // buckets: row-builder items, in chunks of 1024 buckets
+    uint32_t carry = 0, nbig = 0;
+    for (uint32_t b0 = 0; b0 < F; b0 += 1024) {
+        const uint32_t b = b0 + threadIdx.x;
+        uint32_t items = 0;
+        bool big = false;
+        if (b < F) {
+            const uint64_t m = bucket_base[b + 1] - bucket_base[b];
+            big = m > 2 * target;
+            items = big ? (uint32_t)((m + kBigChunk - 1) / kBigChunk) : 1u;
+        }
+        uint32_t tot;
+        const uint32_t pre = block_excl_scan<uint32_t>(items, tmp, &tot);
+        if (b < F) r_pre[b] = carry + pre;
         carry += tot;
+        const uint32_t nb = __syncthreads_count(big);
+        const uint32_t bpre = block_excl_scan<uint32_t>(big ? 1u : 0u, tmp, &tot);
+        if (big) big_list[nbig + bpre] = b;
+        nbig += nb;
+    }
+    if (threadIdx.x == 0) {
+        r_pre[F] = carry;
+        pp->r_items = carry;
+        pp->big = nbig;
     }
 }
 
-// scatter: each pair into both rows; hot rows at the block's reserved range
-// (same grid and pair-to-block assignment as count_kernel).
-__global__ void __launch_bounds__(256) scatter_kernel(uint32_t n, uint64_t m_raw, const uint32_t* __restrict__ src,
-                                                      const uint32_t* __restrict__ dst,
-                                                      const uint64_t* __restrict__ start, uint32_t* __restrict__ fill,
-                                                      const uint32_t* __restrict__ hot_ids,
-                                                      const uint32_t* __restrict__ hot_n_p,
-                                                      const uint32_t* __restrict__ blk, uint32_t* __restrict__ tmp) {
-    __shared__ HotTable t;
-    const uint32_t hot_n = *hot_n_p;
-    hot_build(t, hot_ids, hot_n);
-    const uint32_t* myblk = blk + (uint64_t)blockIdx.x * kHotMax;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_raw;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t u = src[i], v = dst[i];
-        if (u >= n || v >= n || u == v) continue;
-        const int hu = hot_find(t, u), hv = hot_find(t, v);
-        const uint64_t pu = hu >= 0 ? start[u] + myblk[hu] + atomicAdd(&t.local[hu], 1u)
-                                    : start[u] + atomicAdd(&fill[u], 1u);
-        const uint64_t pv = hv >= 0 ? start[v] + myblk[hv] + atomicAdd(&t.local[hv], 1u)
-                                    : start[v] + atomicAdd(&fill[v], 1u);
-        tmp[pu] = v;
-        tmp[pv] = u;
+// Last index i in [0, cnt) with pre[i] <= x (pre ascending, pre[0] = 0).
+__device__ __forceinline__ uint32_t find_item(const uint32_t* __restrict__ pre, uint32_t cnt, uint32_t x) {
+    uint32_t lo = 0, hi = cnt;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= x) lo = mid; else hi = mid;
     }
+    return lo;
+}
+
+// Shared memory of a partition pass: the range -> bucket table, the tile
+// reordered by destination, each slot's destination, and per destination its
+// count, first slot in the tile and reserved global offset.
+struct PartSmem {
+    uint64_t stage[kPartTile];
+    uint16_t dest[kPartTile];
+    uint32_t cnt[256], first[256];
+    unsigned long long base[256];
+    uint32_t scan_tmp[33];
+    uint32_t item;
+};
+
+// Reorder the tile's entries (x[j] to destination d[j], local rank r[j]) by
+// destination and write each destination's run at dst_base[d] + the
+// reservation; every thread of the block calls it.
+__device__ __forceinline__ void part_write(PartSmem& sm, uint32_t ndest, const uint64_t (&x)[kPartPer],
+                                           const uint32_t (&d)[kPartPer], const uint32_t (&rk)[kPartPer],
+                                           const uint64_t* __restrict__ dst_base,
+                                           unsigned long long* __restrict__ dst_fill, uint32_t d_first,
+                                           uint64_t* __restrict__ out) {
+    __syncthreads();  // counts complete
+    uint32_t c = threadIdx.x < ndest ? sm.cnt[threadIdx.x] : 0u;
+    uint32_t tot;
+    const uint32_t f = block_excl_scan<uint32_t>(c, sm.scan_tmp, &tot);
+    if (threadIdx.x < ndest) {
+        sm.first[threadIdx.x] = f;
+        sm.base[threadIdx.x] = c ? dst_base[d_first + threadIdx.x] +
+                                       atomicAdd(&dst_fill[d_first + threadIdx.x], (unsigned long long)c)
+                                 : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t j = 0; j < kPartPer; ++j) {
+        if (d[j] == kPad) continue;
+        const uint32_t pos = sm.first[d[j]] + rk[j];
+        sm.stage[pos] = x[j];
+        sm.dest[pos] = (uint16_t)d[j];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tot; i += kPartTB) {
+        const uint32_t dd = sm.dest[i];
+        out[sm.base[dd] + (i - sm.first[dd])] = sm.stage[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) sm.cnt[threadIdx.x] = 0;
+    __syncthreads();  // counts cleared before the next tile ranks into them
+}
+
+// Pass A: raw pairs -> groups.  Tiles of kPartTile / 2 pairs.
+__global__ void __launch_bounds__(kPartTB, 2) part_pairs_kernel(uint32_t n, uint64_t m_raw,
+                                                                const uint32_t* __restrict__ src,
+                                                                const uint32_t* __restrict__ dst, BucketPlan pl,
+                                                                const uint16_t* __restrict__ range_bucket,
+                                                                const PartPlan* __restrict__ pp,
+                                                                const uint64_t* __restrict__ group_base,
+                                                                unsigned long long* __restrict__ group_fill,
+                                                                uint64_t* __restrict__ E1) {
+    extern __shared__ __align__(16) unsigned char part_smem_raw[];
+    PartSmem& sm = *reinterpret_cast<PartSmem*>(part_smem_raw);
+    uint16_t* tab = reinterpret_cast<uint16_t*>(part_smem_raw + sizeof(PartSmem));
+    for (uint32_t r = threadIdx.x; r < pl.nranges; r += kPartTB) tab[r] = range_bucket[r];
+    if (threadIdx.x < 256) sm.cnt[threadIdx.x] = 0;
+    const uint32_t G = pp->groups;
+    constexpr uint32_t kPairs = kPartTile / 2;
+    const uint64_t ntiles = (m_raw + kPairs - 1) / kPairs;
+    __syncthreads();
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint64_t x[kPartPer];
+        uint32_t d[kPartPer], rk[kPartPer];
+#pragma unroll
+        for (uint32_t j = 0; j < kPartPer / 2; ++j) {
+            const uint64_t i = t * kPairs + (uint64_t)j * kPartTB + threadIdx.x;
+            d[2 * j] = d[2 * j + 1] = kPad;
+            x[2 * j] = x[2 * j + 1] = 0;
+            if (i < m_raw) {
+                const uint32_t u = src[i], v = dst[i];
+                // ids out of range were flagged by the histogram; the call fails after this pass
+                if (u != v && u < n && v < n) {
+                    x[2 * j] = ((uint64_t)u << 32) | v;
+                    x[2 * j + 1] = ((uint64_t)v << 32) | u;
+                    d[2 * j] = tab[u >> pl.rshift] / kGroupFine;
+                    d[2 * j + 1] = tab[v >> pl.rshift] / kGroupFine;
+                    rk[2 * j] = atomicAdd(&sm.cnt[d[2 * j]], 1u);
+                    rk[2 * j + 1] = atomicAdd(&sm.cnt[d[2 * j + 1]], 1u);
+                }
+            }
+        }
+        part_write(sm, G, x, d, rk, group_base, group_fill, 0, E1);
+    }
+}
+
+// Pass B: each group's entries -> its buckets.  Items: kPartTile-entry chunks of a group.
+__global__ void __launch_bounds__(kPartTB, 2) part_groups_kernel(BucketPlan pl, const uint16_t* __restrict__ range_bucket,
+                                                                 const uint32_t* __restrict__ nbp,
+                                                                 const PartPlan* __restrict__ pp,
+                                                                 const uint64_t* __restrict__ group_base,
+                                                                 const uint32_t* __restrict__ b_pre,
+                                                                 const uint64_t* __restrict__ bucket_base,
+                                                                 unsigned long long* __restrict__ bucket_fill,
+                                                                 const uint64_t* __restrict__ E1,
+                                                                 uint64_t* __restrict__ E2) {
+    extern __shared__ __align__(16) unsigned char part_smem_raw[];
+    PartSmem& sm = *reinterpret_cast<PartSmem*>(part_smem_raw);
+    uint16_t* tab = reinterpret_cast<uint16_t*>(part_smem_raw + sizeof(PartSmem));
+    for (uint32_t r = threadIdx.x; r < pl.nranges; r += kPartTB) tab[r] = range_bucket[r];
+    if (threadIdx.x < 256) sm.cnt[threadIdx.x] = 0;
+    const uint32_t F = *nbp, G = pp->groups, items = pp->b_items;
+    __syncthreads();
+    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const uint32_t g = find_item(b_pre, G, it);
+        const uint64_t lo = group_base[g] + (uint64_t)(it - b_pre[g]) * kPartTile;
+        const uint64_t hi = min(group_base[g + 1], lo + kPartTile);
+        const uint32_t f0 = g * kGroupFine;
+        const uint32_t nd = min(kGroupFine, F - f0);
+        uint64_t x[kPartPer];
+        uint32_t d[kPartPer], rk[kPartPer];
+#pragma unroll
+        for (uint32_t j = 0; j < kPartPer; ++j) {
+            const uint64_t e = lo + (uint64_t)j * kPartTB + threadIdx.x;
+            d[j] = kPad;
+            x[j] = 0;
+            if (e < hi) {
+                x[j] = E1[e];
+                d[j] = tab[(uint32_t)(x[j] >> 32) >> pl.rshift] - f0;
+                rk[j] = atomicAdd(&sm.cnt[d[j]], 1u);
+            }
+        }
+        part_write(sm, nd, x, d, rk, bucket_base, bucket_fill, f0, E2);
+    }
+}
+
+// Big buckets, step 1: every kBigChunk-entry chunk counts its owners in
+// shared memory and adds the counts into cnt[] (zero beforehand).  The
+// blocks share out the row builder's items, doing those of big buckets.
+__global__ void __launch_bounds__(kRowsTB) big_count_kernel(const uint32_t* __restrict__ nbp,
+                                                            const PartPlan* __restrict__ pp,
+                                                            const uint32_t* __restrict__ r_pre,
+                                                            const uint32_t* __restrict__ bucket_v0,
+                                                            const uint64_t* __restrict__ bucket_base,
+                                                            const uint64_t* __restrict__ E2, uint32_t* __restrict__ cnt) {
+    extern __shared__ uint32_t cs[];
+    const uint32_t F = *nbp, items = pp->r_items;
+    const uint64_t target = pp->target;
+    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const uint32_t b = find_item(r_pre, F, it);
+        const uint64_t e0 = bucket_base[b], e1 = bucket_base[b + 1];
+        if (e1 - e0 <= 2 * target) continue;  // a small bucket: counted by the row builder
+        const uint32_t v0 = bucket_v0[b], v1 = bucket_v0[b + 1];
+        const uint64_t lo = e0 + (uint64_t)(it - r_pre[b]) * kBigChunk;
+        const uint64_t hi = min(e1, lo + kBigChunk);
+        for (uint32_t a = v0; a < v1; a += min(kSpanMax, v1 - a)) {
+            const uint32_t len = min(kSpanMax, v1 - a);
+            for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) cs[i] = 0;
+            __syncthreads();
+            for (uint64_t e = lo + threadIdx.x; e < hi; e += kRowsTB) {
+                const uint32_t o = (uint32_t)(E2[e] >> 32) - a;
+                if (o < len) atomicAdd(&cs[o], 1u);
+            }
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < len; i += kRowsTB)
+                if (cs[i]) atomicAdd(&cnt[a + i], cs[i]);
+            __syncthreads();
+        }
+    }
+}
+
+// Big buckets, step 2: one block per big bucket turns its counts into row
+// starts (start[v]), clears the cursors and classifies the rows.
+__global__ void __launch_bounds__(kRowsTB) big_starts_kernel(const PartPlan* __restrict__ pp,
+                                                             const uint32_t* __restrict__ big_list,
+                                                             const uint32_t* __restrict__ bucket_v0,
+                                                             const uint64_t* __restrict__ bucket_base,
+                                                             const uint32_t* __restrict__ cnt,
+                                                             uint64_t* __restrict__ start, uint32_t* __restrict__ fill,
+                                                             IngestCtl* ctl) {
+    __shared__ uint64_t scan64[33];
+    __shared__ uint32_t cls[kClasses];
+    __shared__ unsigned long long giant;
+    if (threadIdx.x < kClasses) cls[threadIdx.x] = 0;
+    if (threadIdx.x == 0) giant = 0;
+    __syncthreads();
+    const uint32_t nbig = pp->big;
+    for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const uint32_t b = big_list[bi];
+        const uint32_t v0 = bucket_v0[b], v1 = bucket_v0[b + 1];
+        uint64_t run0 = bucket_base[b];
+        for (uint32_t c0 = v0; c0 < v1; c0 += kRowsTB) {
+            const uint32_t v = c0 + threadIdx.x;
+            const uint32_t c = v < v1 ? cnt[v] : 0u;
+            uint64_t tot;
+            const uint64_t pre = block_excl_scan<uint64_t>((uint64_t)c, scan64, &tot);
+            if (v < v1) {
+                start[v] = run0 + pre;
+                fill[v] = 0;
+                const int k = row_class(c);
+                if (k >= 0) atomicAdd(&cls[k], 1u);
+                if (k == kGiant) atomicAdd(&giant, (unsigned long long)c);
+            }
+            run0 += tot;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses && cls[threadIdx.x]) atomicAdd(&ctl->cls_count[threadIdx.x], cls[threadIdx.x]);
+    if (threadIdx.x == 0 && giant) atomicAdd(&ctl->giant_entries, giant);
+}
+
+// Row builder.  Items (from a device counter): a small bucket is one item --
+// its owners are counted, their row starts written (start[v], cnt[v]) and
+// their neighbours placed in tmp, kSpanMax owners at a time, with counts and
+// cursors in shared memory, writes staying inside the bucket's region; a
+// big bucket is one item per kBigChunk entries -- the chunk counts its
+// owners, reserves its share of each owner's row (fill[v]) and places its
+// entries there.
+__global__ void __launch_bounds__(kRowsTB) bucket_rows_kernel(const uint32_t* __restrict__ nbp,
+                                                              const PartPlan* __restrict__ pp,
+                                                              const uint32_t* __restrict__ r_pre,
+                                                              const uint32_t* __restrict__ bucket_v0,
+                                                              const uint64_t* __restrict__ bucket_base,
+                                                              const uint64_t* __restrict__ E2,
+                                                              uint32_t* __restrict__ cnt, uint64_t* __restrict__ start,
+                                                              uint32_t* __restrict__ fill, uint32_t* __restrict__ tmp,
+                                                              uint32_t* __restrict__ ticket, IngestCtl* ctl) {
+    extern __shared__ uint32_t cs[];  // kSpanMax counters / cursors
+    __shared__ uint64_t scan64[33];
+    __shared__ uint32_t s_it;
+    __shared__ uint32_t cls[kClasses];
+    __shared__ unsigned long long giant;
+    constexpr uint32_t kPer = kSpanMax / kRowsTB;
+    const uint32_t F = *nbp, items = pp->r_items;
+    const uint64_t target = pp->target;
+    if (threadIdx.x < kClasses) cls[threadIdx.x] = 0;
+    if (threadIdx.x == 0) giant = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_it = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const uint32_t it = s_it;
+        if (it >= items) break;
+        const uint32_t b = find_item(r_pre, F, it);
+        const uint32_t v0 = bucket_v0[b], v1 = bucket_v0[b + 1];
+        const uint64_t e0 = bucket_base[b], e1 = bucket_base[b + 1];
+        if (e1 - e0 > 2 * target) {
+            // ---- a chunk of a big bucket
+            const uint64_t lo = e0 + (uint64_t)(it - r_pre[b]) * kBigChunk;
+            const uint64_t hi = min(e1, lo + kBigChunk);
+            for (uint32_t a = v0; a < v1; a += min(kSpanMax, v1 - a)) {
+                const uint32_t len = min(kSpanMax, v1 - a);
+                for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) cs[i] = 0;
+                __syncthreads();
+                for (uint64_t e = lo + threadIdx.x; e < hi; e += kRowsTB) {
+                    const uint32_t o = (uint32_t)(E2[e] >> 32) - a;
+                    if (o < len) atomicAdd(&cs[o], 1u);
+                }
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) {
+                    const uint32_t c = cs[i];
+                    if (c) cs[i] = atomicAdd(&fill[a + i], c);  // this chunk's first slot in the row
+                }
+                __syncthreads();
+                for (uint64_t e = lo + threadIdx.x; e < hi; e += kRowsTB) {
+                    const uint64_t x = E2[e];
+                    const uint32_t o = (uint32_t)(x >> 32) - a;
+                    if (o < len) tmp[start[a + o] + atomicAdd(&cs[o], 1u)] = (uint32_t)x;
+                }
+                __syncthreads();
+            }
+            continue;
+        }
+        // ---- a small bucket, whole
+        uint64_t sub_base = e0;
+        for (uint32_t a = v0; a < v1; a += min(kSpanMax, v1 - a)) {
+            const uint32_t len = min(kSpanMax, v1 - a);
+            for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) cs[i] = 0;
+            __syncthreads();
+            for (uint64_t e = e0 + threadIdx.x; e < e1; e += kRowsTB) {
+                const uint32_t o = (uint32_t)(E2[e] >> 32) - a;
+                if (o < len) atomicAdd(&cs[o], 1u);
+            }
+            __syncthreads();
+            // exclusive scan of the counts: each thread kPer consecutive owners
+            uint64_t mine = 0;
+            for (uint32_t j = 0; j < kPer; ++j) {
+                const uint32_t i = threadIdx.x * kPer + j;
+                if (i < len) mine += cs[i];
+            }
+            uint64_t sub_total;
+            uint64_t run = block_excl_scan<uint64_t>(mine, scan64, &sub_total);
+            for (uint32_t j = 0; j < kPer; ++j) {
+                const uint32_t i = threadIdx.x * kPer + j;
+                if (i >= len) break;
+                const uint32_t c = cs[i];
+                cnt[a + i] = c;
+                start[a + i] = sub_base + run;
+                cs[i] = (uint32_t)run;  // cursor, relative to sub_base
+                // the row's sort class (rows of at most 32 entries are sorted by class -1)
+                const int k = row_class(c);
+                if (k >= 0) atomicAdd(&cls[k], 1u);
+                if (k == kGiant) atomicAdd(&giant, (unsigned long long)c);
+                run += c;
+            }
+            __syncthreads();
+            for (uint64_t e = e0 + threadIdx.x; e < e1; e += kRowsTB) {
+                const uint64_t x = E2[e];
+                const uint32_t o = (uint32_t)(x >> 32) - a;
+                if (o < len) tmp[sub_base + atomicAdd(&cs[o], 1u)] = (uint32_t)x;
+            }
+            sub_base += sub_total;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses && cls[threadIdx.x]) atomicAdd(&ctl->cls_count[threadIdx.x], cls[threadIdx.x]);
+    if (threadIdx.x == 0 && giant) atomicAdd(&ctl->giant_entries, giant);
 }
 
 // ----------------------------------------------------------- row sort
-
-__global__ void classify_count(uint32_t n, const uint32_t* __restrict__ cnt, IngestCtl* ctl) {
-    __shared__ uint32_t c[kClasses];
-    __shared__ unsigned long long giant;
-    if (threadIdx.x < kClasses) c[threadIdx.x] = 0;
-    if (threadIdx.x == 0) giant = 0;
-    __syncthreads();
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t len = cnt[v];
-        int k = row_class(len);
-        if (k >= 0) atomicAdd(&c[k], 1u);
-        if (k == kGiant) atomicAdd(&giant, (unsigned long long)len);
-    }
-    __syncthreads();
-    if (threadIdx.x < kClasses && c[threadIdx.x]) atomicAdd(&ctl->cls_count[threadIdx.x], c[threadIdx.x]);
-    if (threadIdx.x == 0 && giant) atomicAdd(&ctl->giant_entries, giant);
-}
 
 struct ClassLists {
     uint32_t* rows;             // all class lists, back to back
@@ -614,115 +902,119 @@ __global__ void __launch_bounds__(kBlockWarps * 32) sort_block_rows(const uint32
     }
 }
 
-// ---- giant rows (> 8192 entries): partition each row by value window of
-// kWin ids (a counting sort on value >> kWinBits), then de-duplicate and order
-// each window with a kWin-bit bitmap in shared memory.
+// ---- giant rows (> kBlockRowMax entries): one block per row sorts it by an
+// LSD radix sort on 8-bit digits of the neighbour ids (as many passes as n's
+// ids need), ping-ponging between the row's place in tmp and in spare.  Each
+// pass is stable: a digit histogram of the row gives every digit's first
+// slot, then the row is walked in order one block-sized tile at a time, and
+// a key's slot is its digit's next free slot plus the number of earlier keys
+// of the tile with the same digit (warp match within a warp, per-warp digit
+// counts across warps).  The sorted row is then de-duplicated into tmp.
+constexpr uint32_t kRadixTB = 1024;
+constexpr uint32_t kRadixWarps = kRadixTB / 32;
 
-// window histogram; grid.y walks giant rows, grid.x chunks of a row
-__global__ void giant_hist(const uint32_t* __restrict__ list, uint32_t count, const uint64_t* __restrict__ start,
-                           const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ tmp, uint32_t nwin,
-                           uint32_t* __restrict__ hist) {
-    extern __shared__ uint32_t sh[];
-    const bool use_smem = nwin <= 4096;
-    for (uint32_t r = blockIdx.y; r < count; r += gridDim.y) {
-        uint32_t v = list[r];
-        uint32_t len = cnt[v];
-        uint64_t b = start[v];
-        uint32_t* h = hist + (uint64_t)r * nwin;
-        if (use_smem) {
-            for (uint32_t i = threadIdx.x; i < nwin; i += blockDim.x) sh[i] = 0;
-            __syncthreads();
-        }
-        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
-            uint32_t wv = tmp[b + i] >> kWinBits;
-            if (use_smem) atomicAdd(&sh[wv], 1u);
-            else atomicAdd(&h[wv], 1u);
-        }
-        if (use_smem) {
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < nwin; i += blockDim.x)
-                if (sh[i]) atomicAdd(&h[i], sh[i]);
-            __syncthreads();
-        }
-    }
-}
+struct RadixSmem {
+    uint32_t base[256];                // next free slot of each digit
+    uint32_t wcnt[kRadixWarps][256];   // per-warp digit counts of a tile, then their exclusive prefixes
+    uint32_t scan_tmp[33];
+    uint32_t row, kept;
+};
 
-__global__ void giant_scatter(const uint32_t* __restrict__ list, uint32_t count, const uint64_t* __restrict__ start,
-                              const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ tmp, uint32_t nwin,
-                              const uint64_t* __restrict__ hoff, uint32_t* __restrict__ cursor,
-                              uint32_t* __restrict__ spare) {
-    for (uint32_t r = blockIdx.y; r < count; r += gridDim.y) {
-        uint32_t v = list[r];
-        uint32_t len = cnt[v];
-        uint64_t b = start[v];
-        const uint64_t* ho = hoff + (uint64_t)r * nwin;
-        uint32_t* cur = cursor + (uint64_t)r * nwin;
-        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
-            uint32_t x = tmp[b + i];
-            uint32_t wv = x >> kWinBits;
-            spare[b + (ho[wv] - ho[0]) + atomicAdd(&cur[wv], 1u)] = x;
-        }
-    }
-}
-
-// one warp per (row, window); EMIT = false counts the window's distinct
-// values into ucnt, EMIT = true writes them in order at their row position
-template <bool EMIT>
-__global__ void __launch_bounds__(256) giant_windows(const uint32_t* __restrict__ list, uint32_t count,
-                                                     const uint64_t* __restrict__ start, uint32_t nwin,
-                                                     const uint32_t* __restrict__ hist,
-                                                     const uint64_t* __restrict__ hoff,
-                                                     const uint32_t* __restrict__ spare, uint32_t* __restrict__ ucnt,
-                                                     const uint64_t* __restrict__ uoff, uint32_t* __restrict__ tmp,
-                                                     uint32_t* __restrict__ newlen) {
-    __shared__ uint32_t bm[8][kWinWords];
-    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    const uint64_t total = (uint64_t)count * nwin;
-    for (uint64_t it = (uint64_t)blockIdx.x * 8 + w; it < total; it += (uint64_t)gridDim.x * 8) {
-        uint32_t r = (uint32_t)(it / nwin), wi = (uint32_t)(it % nwin);
-        uint32_t v = list[r];
-        uint64_t b = start[v];
-        const uint64_t* ho = hoff + (uint64_t)r * nwin;
-        if (EMIT && wi == 0 && lane == 0) newlen[v] = (uint32_t)(uoff[(uint64_t)r * nwin + nwin] - uoff[(uint64_t)r * nwin]);
-        uint32_t h = hist[it];
-        if (h == 0) {
-            if (!EMIT && lane == 0) ucnt[it] = 0;  // every window's count feeds the scan
-            continue;
-        }
-#pragma unroll
-        for (uint32_t q = 0; q < kWinWords / 32; ++q) bm[w][q * 32 + lane] = 0;
-        __syncwarp();
-        uint64_t seg = b + (ho[wi] - ho[0]);
-        for (uint32_t i = lane; i < h; i += 32) {
-            uint32_t x = spare[seg + i] & (kWin - 1);
-            atomicOr(&bm[w][x >> 5], 1u << (x & 31));
-        }
-        __syncwarp();
-        // lane owns words [lane * 8, lane * 8 + 8)
-        uint32_t words[kWinWords / 32], c = 0;
-#pragma unroll
-        for (uint32_t q = 0; q < kWinWords / 32; ++q) {
-            words[q] = bm[w][lane * (kWinWords / 32) + q];
-            c += __popc(words[q]);
-        }
-        if (!EMIT) {
-            uint32_t tot = warp_sum(c);
-            if (lane == 0) ucnt[it] = tot;
-        } else {
-            uint32_t inc = warp_incl_scan(c);
-            uint64_t pos = b + (uoff[it] - uoff[(uint64_t)r * nwin]) + (inc - c);
-            uint32_t vbase = wi * kWin + lane * (kWinWords / 32) * 32;
-#pragma unroll
-            for (uint32_t q = 0; q < kWinWords / 32; ++q) {
-                uint32_t m = words[q];
-                while (m) {
-                    uint32_t bit = __ffs(m) - 1;
-                    m &= m - 1;
-                    tmp[pos++] = vbase + q * 32 + bit;
-                }
+__global__ void __launch_bounds__(kRadixTB) giant_radix_kernel(const uint32_t* __restrict__ list, uint32_t count,
+                                                               const uint64_t* __restrict__ start,
+                                                               const uint32_t* __restrict__ cnt,
+                                                               uint32_t* __restrict__ tmp,
+                                                               uint32_t* __restrict__ spare, uint32_t passes,
+                                                               uint32_t* __restrict__ newlen,
+                                                               uint32_t* __restrict__ ticket) {
+    __shared__ RadixSmem sm;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
+    for (uint32_t i = tid; i < kRadixWarps * 256; i += kRadixTB) (&sm.wcnt[0][0])[i] = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sm.row = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const uint32_t r = sm.row;
+        if (r >= count) break;
+        const uint32_t v = list[r];
+        const uint32_t len = cnt[v];
+        uint32_t* A = tmp + start[v];
+        uint32_t* B = spare + start[v];
+        for (uint32_t pass = 0; pass < passes; ++pass) {
+            const uint32_t shift = 8 * pass;
+            if (tid < 256) sm.base[tid] = 0;
+            __syncthreads();
+            for (uint32_t i0 = 0; i0 < len; i0 += kRadixTB) {
+                const uint32_t i = i0 + tid;
+                const uint32_t d = i < len ? (A[i] >> shift) & 255u : 256u;
+                const uint32_t peers = __match_any_sync(kFullMask, d);
+                if (d < 256u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sm.base[d], (uint32_t)__popc(peers));
             }
+            __syncthreads();
+            // exclusive scan of the 256 digit counts: warps 0..7 scan their 32
+            // digits, then add the totals of the warps before them
+            uint32_t cnt_d = 0, inc_d = 0;
+            if (tid < 256) {
+                cnt_d = sm.base[tid];
+                inc_d = warp_incl_scan(cnt_d);
+                if (lane == 31) sm.scan_tmp[w] = inc_d;
+            }
+            __syncthreads();
+            if (tid < 256) {
+                uint32_t add = 0;
+                for (uint32_t q = 0; q < w; ++q) add += sm.scan_tmp[q];
+                sm.base[tid] = add + inc_d - cnt_d;
+            }
+            __syncthreads();
+            for (uint32_t i0 = 0; i0 < len; i0 += kRadixTB) {
+                const uint32_t i = i0 + tid;
+                const bool valid = i < len;
+                const uint32_t key = valid ? A[i] : 0u;
+                const uint32_t d = valid ? (key >> shift) & 255u : 256u;
+                const uint32_t peers = __match_any_sync(kFullMask, d);
+                const uint32_t rank = __popc(peers & lanemask_lt());
+                if (valid && lane == (uint32_t)(__ffs(peers) - 1)) sm.wcnt[w][d] = __popc(peers);
+                __syncthreads();
+                uint32_t col = 0;
+                if (tid < 256) {  // per digit: exclusive prefix over the warps, in place
+                    for (uint32_t q = 0; q < kRadixWarps; ++q) {
+                        const uint32_t c = sm.wcnt[q][tid];
+                        sm.wcnt[q][tid] = col;
+                        col += c;
+                    }
+                }
+                __syncthreads();
+                if (valid) B[sm.base[d] + sm.wcnt[w][d] + rank] = key;
+                __syncthreads();
+                if (tid < 256) {
+                    sm.base[tid] += col;
+                    for (uint32_t q = 0; q < kRadixWarps; ++q) sm.wcnt[q][tid] = 0;
+                }
+                __syncthreads();
+            }
+            uint32_t* t = A;
+            A = B;
+            B = t;
         }
-        __syncwarp();
+        // A holds the sorted row: keep the first of each run of equal ids, in
+        // tmp (in place when A is tmp: a tile is read whole before any of its
+        // writes, which land at or below the tile's own positions)
+        uint32_t* out = tmp + start[v];
+        uint32_t kept = 0, prev_last = kPad;
+        for (uint32_t i0 = 0; i0 < len; i0 += kRadixTB) {
+            const uint32_t i = i0 + tid;
+            const uint32_t key = i < len ? A[i] : kPad;
+            const uint32_t before = i == i0 ? prev_last : (i - 1 < len ? A[i - 1] : kPad);
+            const uint32_t last = A[min(len, i0 + kRadixTB) - 1];
+            const bool keep = i < len && key != before;
+            uint32_t tot;
+            const uint32_t pos = block_excl_scan<uint32_t>(keep ? 1u : 0u, sm.scan_tmp, &tot);
+            if (keep) out[kept + pos] = key;
+            kept += tot;
+            prev_last = last;
+            __syncthreads();
+        }
+        if (tid == 0) newlen[v] = kept;
     }
 }
 
@@ -775,55 +1067,114 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     DSG_TRY_CUDA(sc.get(&sums, nt));
     DSG_TRY_CUDA(sc.get(&newlen, (size_t)n + 1));
     DSG_TRY_CUDA(sc.get(&ctl, 1));
-    DSG_TRY_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)n + 1) * 4, s));
     DSG_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(IngestCtl), s));
-    // count and scatter run on the same grid, so each block meets the same pairs
-    const uint32_t pair_grid = (uint32_t)std::min<uint64_t>((m_raw + 255) / 256 + 1, (uint64_t)dev_info().sms * 8);
-    // small inputs skip the hot-endpoint pass: no address is hit often enough
-    // to matter, and its fixed cost would dominate
-    const bool hot_pass = m_raw >= kHotPassMinPairs;
-    uint32_t *hot_ids, *hot_n, *blk;
-    DSG_TRY_CUDA(sc.get(&hot_ids, kHotMax));
-    DSG_TRY_CUDA(sc.get(&hot_n, 1));
-    DSG_TRY_CUDA(sc.get(&blk, hot_pass ? (size_t)pair_grid * kHotMax : 1));
-    if (hot_pass) {
-        const size_t smem = 2 * kSampleSlots * sizeof(uint32_t);
-        static bool smem_set[64] = {};  // the attribute is per function and device, set once (idempotent)
+    DSG_TRY_CUDA(cudaMemsetAsync(newlen, 0, ((size_t)n + 1) * 4, s));
+    const uint32_t sms = (uint32_t)dev_info().sms;
+    // ---- buckets of consecutive owners, from an exact histogram over vertex ranges
+    const BucketPlan pl = bucket_plan_for(n);
+    const uint64_t cap = 2 * m_raw;  // directed entries at most
+    uint32_t *range_cnt, *bucket_v0, *nb, *ticket, *b_pre, *r_pre, *big_list, *fill;
+    uint16_t* range_bucket;
+    uint64_t *bucket_base, *group_base, *E1, *E2;
+    unsigned long long *bucket_fill, *group_fill, *maxb;
+    PartPlan* pp;
+    DSG_TRY_CUDA(sc.get(&range_cnt, pl.nranges ? pl.nranges : 1));
+    DSG_TRY_CUDA(sc.get(&range_bucket, pl.nranges ? pl.nranges : 1));
+    // buckets never outnumber the ranges (each starts at a range)
+    const size_t fcap = std::min<size_t>(kBucketsMax, (size_t)pl.nranges + 1);
+    const size_t gcap = (fcap + kGroupFine - 1) / kGroupFine;
+    DSG_TRY_CUDA(sc.get(&bucket_v0, fcap + 1));
+    DSG_TRY_CUDA(sc.get(&bucket_base, fcap + 1));
+    DSG_TRY_CUDA(sc.get(&bucket_fill, fcap));
+    DSG_TRY_CUDA(sc.get(&group_base, gcap + 1));
+    DSG_TRY_CUDA(sc.get(&group_fill, gcap));
+    DSG_TRY_CUDA(sc.get(&b_pre, gcap + 1));
+    DSG_TRY_CUDA(sc.get(&r_pre, fcap + 1));
+    DSG_TRY_CUDA(sc.get(&big_list, fcap));
+    DSG_TRY_CUDA(sc.get(&pp, 1));
+    DSG_TRY_CUDA(sc.get(&nb, 2));
+    DSG_TRY_CUDA(sc.get(&maxb, 1));
+    ticket = nb + 1;
+    DSG_TRY_CUDA(sc.get(&E1, cap ? cap : 1));
+    DSG_TRY_CUDA(sc.get(&E2, cap ? cap : 1));
+    DSG_TRY_CUDA(sc.get(&tmp, cap ? cap : 1));
+    DSG_TRY_CUDA(sc.get(&fill, (size_t)n + 1));
+    DSG_TRY_CUDA(cudaMemsetAsync(range_cnt, 0, (size_t)(pl.nranges ? pl.nranges : 1) * 4, s));
+    DSG_TRY_CUDA(cudaMemsetAsync(bucket_fill, 0, fcap * 8, s));
+    DSG_TRY_CUDA(cudaMemsetAsync(group_fill, 0, gcap * 8, s));
+    DSG_TRY_CUDA(cudaMemsetAsync(nb, 0, 2 * sizeof(uint32_t), s));
+    DSG_TRY_CUDA(cudaMemsetAsync(maxb, 0, sizeof(unsigned long long), s));
+    DSG_TRY_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)n + 1) * 4, s));  // big buckets add their counts into it
+    const size_t hist_smem = (size_t)pl.nranges * 4;
+    const size_t part_smem = sizeof(PartSmem) + (((size_t)pl.nranges * 2 + 15) & ~size_t(15));
+    const size_t rows_smem = (size_t)kSpanMax * 4;
+    {
+        static bool smem_set[64] = {};  // the attributes are per function and device, set once (idempotent)
         if (!smem_set[dev & 63]) {
-            DSG_TRY_CUDA(cudaFuncSetAttribute(hot_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int part_max = (int)(sizeof(PartSmem) + (size_t)kRangesMax * 2);
+            DSG_TRY_CUDA(cudaFuncSetAttribute(range_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(kRangesMax * 4)));
+            DSG_TRY_CUDA(cudaFuncSetAttribute(part_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, part_max));
+            DSG_TRY_CUDA(cudaFuncSetAttribute(part_groups_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              part_max));
+            DSG_TRY_CUDA(cudaFuncSetAttribute(big_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)rows_smem));
+            DSG_TRY_CUDA(cudaFuncSetAttribute(bucket_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)rows_smem));
             smem_set[dev & 63] = true;
         }
-        uint2* sample;
-        DSG_TRY_CUDA(sc.get(&sample, (size_t)sample_take(m_raw)));
-        {
-            LaunchScope ls_("ingest_hot_gather", s);
-            hot_gather<<<(uint32_t)((sample_take(m_raw) + 255) / 256), 256, 0, s>>>(m_raw, src, dst, sample);
-        }
-        uint2* cand;         // (id, hits) of the frequent sampled endpoints, every part's
-        uint32_t* cand_cnt;  // [0, 256) histogram of their hits, [256] their number
-        DSG_TRY_CUDA(sc.get(&cand, (size_t)kHotParts * kSampleSlots));
-        DSG_TRY_CUDA(sc.get(&cand_cnt, 257));
-        DSG_TRY_CUDA(cudaMemsetAsync(cand_cnt, 0, 257 * sizeof(uint32_t), s));
-        {
-            LaunchScope ls_("ingest_hot_sample", s);
-            hot_sample<<<kHotParts, 1024, smem, s>>>(n, m_raw, sample, cand, cand_cnt + 256, cand_cnt);
-        }
-        {
-            LaunchScope ls_("ingest_hot_select", s);
-            hot_select<<<1, 1024, 0, s>>>(cand, cand_cnt + 256, cand_cnt, hot_ids, hot_n);
-        }
-    } else {
-        DSG_TRY_CUDA(cudaMemsetAsync(hot_n, 0, 4, s));
     }
-    { LaunchScope ls_("ingest_count_kernel", s); count_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, cnt, hot_ids, hot_n, blk, ctl); }
-    DSG_TRY_CUDA(cudaGetLastError());
-    if (hot_pass) {
-        LaunchScope ls_("ingest_hot_bases", s);
-        hot_block_bases<<<kHotMax, 256, 0, s>>>(hot_n, pair_grid, blk);
+    if (m_raw) {
+        const uint32_t g = (uint32_t)std::min<uint64_t>((m_raw + 65535) / 65536, sms);
+        LaunchScope ls_("ingest_range_hist", s);
+        range_hist_kernel<<<g, 1024, hist_smem, s>>>(n, m_raw, src, dst, pl, range_cnt, ctl);
     }
     DSG_TRY_CUDA(cudaGetLastError());
-    DSG_TRY_CUDA(device_scan(cnt, n, start, sums, s));
-    { LaunchScope ls_("ingest_classify_count", s); classify_count<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, ctl); }
+    {
+        LaunchScope ls_("ingest_bucket_plan", s);
+        bucket_plan_kernel<<<1, 1024, 0, s>>>(n, range_cnt, pl, range_bucket, bucket_v0, bucket_base, start, nb,
+                                              maxb);
+    }
+    DSG_TRY_CUDA(cudaGetLastError());
+    {
+        LaunchScope ls_("ingest_part_plan", s);
+        part_plan_kernel<<<1, 1024, 0, s>>>(nb, bucket_base, group_base, b_pre, r_pre, big_list, pp);
+    }
+    DSG_TRY_CUDA(cudaGetLastError());
+    int per_sm_rows = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rows, bucket_rows_kernel, kRowsTB, rows_smem) !=
+            cudaSuccess || per_sm_rows < 1)
+        per_sm_rows = 1;
+    if (m_raw) {
+        {
+            LaunchScope ls_("ingest_part_pairs", s);
+            part_pairs_kernel<<<2 * sms, kPartTB, part_smem, s>>>(n, m_raw, src, dst, pl, range_bucket, pp, group_base,
+                                                              group_fill, E1);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+        {
+            LaunchScope ls_("ingest_part_groups", s);
+            part_groups_kernel<<<2 * sms, kPartTB, part_smem, s>>>(pl, range_bucket, nb, pp, group_base, b_pre,
+                                                               bucket_base, bucket_fill, E1, E2);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+        {
+            LaunchScope ls_("ingest_big_count", s);
+            big_count_kernel<<<sms * (uint32_t)per_sm_rows, kRowsTB, rows_smem, s>>>(nb, pp, r_pre, bucket_v0,
+                                                                                    bucket_base, E2, cnt);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+        {
+            LaunchScope ls_("ingest_big_starts", s);
+            big_starts_kernel<<<sms, kRowsTB, 0, s>>>(pp, big_list, bucket_v0, bucket_base, cnt, start, fill, ctl);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+    }
+    {
+        LaunchScope ls_("ingest_bucket_rows", s);
+        bucket_rows_kernel<<<sms * (uint32_t)per_sm_rows, kRowsTB, rows_smem, s>>>(
+            nb, pp, r_pre, bucket_v0, bucket_base, E2, cnt, start, fill, tmp, ticket, ctl);
+    }
     DSG_TRY_CUDA(cudaGetLastError());
     IngestCtl hc;
     uint64_t total = 0;
@@ -840,17 +1191,12 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
         lists.base[c] = nlist;
         nlist += hc.cls_count[c];
     }
-    DSG_TRY_CUDA(sc.get(&tmp, total ? total : 1));
     DSG_TRY_CUDA(sc.get(&lists.rows, nlist ? nlist : 1));
-    DSG_TRY_CUDA(cudaMemsetAsync(newlen, 0, ((size_t)n + 1) * 4, s));  // reused as the fill counter
-    { LaunchScope ls_("ingest_scatter_kernel", s); scatter_kernel<<<pair_grid, 256, 0, s>>>(n, m_raw, src, dst, start, newlen, hot_ids, hot_n, blk, tmp); }
-    DSG_TRY_CUDA(cudaGetLastError());
     {
         LaunchScope ls_("ingest_sort_small_rows", s);
         sort_small_rows<<<grid_for((uint64_t)n, 256), 256, 0, s>>>(n, start, cnt, tmp, newlen, lists, ctl);
     }
     DSG_TRY_CUDA(cudaGetLastError());
-    const uint32_t sms = (uint32_t)dev_info().sms;
     auto warp_grid = [&](uint32_t rows) { return (uint32_t)std::min<uint64_t>((rows + 7) / 8, (uint64_t)sms * 16); };
     if (hc.cls_count[0]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<2><<<warp_grid(hc.cls_count[0]), 256, 0, s>>>(lists.rows + lists.base[0], hc.cls_count[0], start, cnt, tmp, newlen); }
     if (hc.cls_count[1]) { LaunchScope ls_("ingest_sort_warp_rows", s); sort_warp_rows<4><<<warp_grid(hc.cls_count[1]), 256, 0, s>>>(lists.rows + lists.base[1], hc.cls_count[1], start, cnt, tmp, newlen); }
@@ -878,33 +1224,19 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
     if (hc.cls_count[kGiant]) {
         const uint32_t ng = hc.cls_count[kGiant];
         const uint32_t* glist = lists.rows + lists.base[kGiant];
-        const uint32_t nwin = (uint32_t)(((uint64_t)n + kWin - 1) >> kWinBits);
-        const uint64_t pairs = (uint64_t)ng * nwin;
-        uint32_t *hist, *cursor, *ucnt, *spare;
-        uint64_t *hoff, *uoff, *gsums;
-        DSG_TRY_CUDA(sc.get(&spare, total ? total : 1));
-        DSG_TRY_CUDA(sc.get(&hist, pairs));
-        DSG_TRY_CUDA(sc.get(&cursor, pairs));
-        DSG_TRY_CUDA(sc.get(&ucnt, pairs));
-        DSG_TRY_CUDA(sc.get(&hoff, pairs + 1));
-        DSG_TRY_CUDA(sc.get(&uoff, pairs + 1));
-        DSG_TRY_CUDA(sc.get(&gsums, pairs / kScanTile + 2));
-        DSG_TRY_CUDA(cudaMemsetAsync(hist, 0, pairs * 4, s));
-        DSG_TRY_CUDA(cudaMemsetAsync(cursor, 0, pairs * 4, s));
-        dim3 grid(32, std::min<uint32_t>(ng, 65535u));
-        size_t smem = nwin <= 4096 ? (size_t)nwin * 4 : 0;
-        { LaunchScope ls_("ingest_giant_rows", s); giant_hist<<<grid, 256, smem, s>>>(glist, ng, start, cnt, tmp, nwin, hist); }
-        DSG_TRY_CUDA(cudaGetLastError());
-        DSG_TRY_CUDA(device_scan(hist, pairs, hoff, gsums, s));
-        { LaunchScope ls_("ingest_giant_rows", s); giant_scatter<<<grid, 256, 0, s>>>(glist, ng, start, cnt, tmp, nwin, hoff, cursor, spare); }
-        DSG_TRY_CUDA(cudaGetLastError());
-        uint32_t wg = (uint32_t)std::min<uint64_t>((pairs + 7) / 8, (uint64_t)sms * 32);
-        { LaunchScope ls_("ingest_giant_rows", s); giant_windows<false><<<wg, 256, 0, s>>>(glist, ng, start, nwin, hist, hoff, spare, ucnt, nullptr, tmp, newlen); }
-        DSG_TRY_CUDA(cudaGetLastError());
-        DSG_TRY_CUDA(device_scan(ucnt, pairs, uoff, gsums, s));
-        { LaunchScope ls_("ingest_giant_rows", s); giant_windows<true><<<wg, 256, 0, s>>>(glist, ng, start, nwin, hist, hoff, spare, ucnt, uoff, tmp, newlen); }
-        DSG_TRY_CUDA(cudaGetLastError());
+        uint32_t nbits = 1;
+        while (nbits < 32 && ((uint64_t)n - 1) >> nbits) ++nbits;
+        const uint32_t passes = (nbits + 7) / 8;
+        // the bucket entries are no longer needed: their space is the radix sort's spare buffer
+        uint32_t* spare = reinterpret_cast<uint32_t*>(E1);
+        uint32_t* gticket;
+        DSG_TRY_CUDA(sc.get(&gticket, 1));
+        DSG_TRY_CUDA(cudaMemsetAsync(gticket, 0, sizeof(uint32_t), s));
+        const uint32_t g = std::min<uint32_t>(ng, sms);
+        LaunchScope ls_("ingest_giant_rows", s);
+        giant_radix_kernel<<<g, kRadixTB, 0, s>>>(glist, ng, start, cnt, tmp, spare, passes, newlen, gticket);
     }
+    DSG_TRY_CUDA(cudaGetLastError());
     dsg_graph* g = new dsg_graph();
     g->n = n;
     g->device = dev;

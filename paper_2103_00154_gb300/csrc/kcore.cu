@@ -49,6 +49,8 @@
 // after its contents, so a stale slot is never taken for a new one.
 #include <string.h>
 
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 #include "dsg_common.cuh"
@@ -85,6 +87,7 @@ struct __align__(128) CoreCtl {
     unsigned long long levels;
     unsigned long long dbg[4];   // bounds-check builds: first bad access (site, index, capacity, level)
     unsigned long long stamps;
+    unsigned long long tail;     // the level loop stopped with this many vertices left for the cluster tail
 };
 
 // Bounds checks of the debug build (DSG_DEBUG_BOUNDS): a bad index is
@@ -129,6 +132,7 @@ struct CoreArgs {
     uint32_t local_max;   // rows up to this length found while draining stay in the block
     uint32_t local_work;  // ... while the block's local entries per batch stay within this
     uint32_t inline_max;  // rows up to this length claimed by a block's scan are drained by that block
+    uint32_t tail_max;    // leave the level loop once at most this many vertices remain (0: never)
     uint64_t* trace;      // nullable: block 0 stamps (%globaltimer, kind) at each phase end
     uint64_t trace_cap;
 };
@@ -214,7 +218,7 @@ __device__ __forceinline__ uint64_t queue_row(const CoreArgs& a, CoreLevel* P, u
 }
 
 template <int TB>
-__global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
+__global__ void __launch_bounds__(TB, TB >= 1024 ? 1 : 2) kcore_kernel(CoreArgs a) {
     __shared__ CoreSmem<TB> sm;
     CoreCtl* ctl = a.ctl;
     const uint32_t tid = threadIdx.x;
@@ -593,6 +597,12 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
         visited += lvl_claimed;
         ++level;
         if (visited >= n) break;
+        if (a.tail_max && (uint64_t)n - visited <= a.tail_max) {
+            // few vertices remain: the cluster finishes them on the compacted graph
+            // (every block sees the same totals, so all leave here together)
+            if (blockIdx.x == 0 && tid == 0) ctl->tail = (uint64_t)n - visited;
+            break;
+        }
         if (level_min == 0xffffffffu || level_min <= k) {
             // nothing left above k yet visited < n: cannot happen on valid input
             if (blockIdx.x == 0 && tid == 0) atomicOr(&ctl->err, ERR_CAPACITY);
@@ -638,6 +648,7 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     a.local_max = tu.local_max;
     a.local_work = tu.local_work;
     a.inline_max = tu.inline_max;
+    a.tail_max = g->no_tail ? 0 : (tu.tail_max < kTailMaxVertices ? tu.tail_max : kTailMaxVertices);
     a.trace = trace_dev;
     a.trace_cap = trace_cap;
     uint32_t grid = 1;
@@ -687,18 +698,30 @@ dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, ui
     DSG_TRY_CUDA(e);
     CoreCtl c;
     DSG_TRY_CUDA(cudaMemcpyAsync(&c, a.ctl, sizeof(CoreCtl), cudaMemcpyDeviceToHost, s));
-    if (!direct) DSG_TRY_CUDA(copy_any(core_out, a.deg, (size_t)n * 4, s));
     DSG_TRY_CUDA(cudaStreamSynchronize(s));
     if (c.dbg[0]) {
         set_error("kcore bounds check: site %llu index %llu capacity %llu level %llu", c.dbg[0], c.dbg[1], c.dbg[2],
                   c.dbg[3]);
         return DSG_ECUDA;
     }
+    dsg_status st = status_from_err(c.err, "kcore");
+    if (st != DSG_OK) return st;
     if (stamps) *stamps = c.stamps;
     // levels, queued pieces, remaining vertices scanned / written, degree atomics
-    const uint64_t vals[5] = {c.levels, c.pieces, c.rem_scanned, c.rem_written, c.atomics};
+    uint64_t vals[5] = {c.levels, c.pieces, c.rem_scanned, c.rem_written, c.atomics};
+    if (c.tail) {
+        // a traced run's tail stamps follow the grid kernel's
+        const uint64_t used = trace_dev ? std::min<uint64_t>(2 * c.stamps, trace_cap) : 0;
+        uint64_t tail_stamps = 0;
+        st = kcore_tail(n, g->off, g->adj, a.deg, a.claim, (uint32_t)c.tail, s, vals,
+                        trace_dev ? trace_dev + used : nullptr, trace_dev ? trace_cap - used : 0, &tail_stamps);
+        if (st != DSG_OK) return st;
+        if (stamps) *stamps += tail_stamps;
+    }
+    if (!direct) DSG_TRY_CUDA(copy_any(core_out, a.deg, (size_t)n * 4, s));
+    DSG_TRY_CUDA(cudaStreamSynchronize(s));
     for (uint32_t i = 0; stats && i < nstats && i < 5; ++i) stats[i] = vals[i];
-    return status_from_err(c.err, "kcore");
+    return DSG_OK;
 }
 
 }  // namespace dsg

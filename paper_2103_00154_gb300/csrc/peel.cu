@@ -51,6 +51,7 @@ struct __align__(128) PeelCtl {
     unsigned long long pad7[15];
     unsigned long long rounds, best_round, best_E, best_V;
     unsigned long long stamps;
+    unsigned long long cur_S, cur_E;  // |S_r| and |E(S_r)| where the launch stopped
 };
 
 struct PeelArgs {
@@ -74,6 +75,11 @@ struct PeelArgs {
     uint32_t hot_deg;
     uint64_t* trace;      // nullable: block 0 stamps %globaltimer after every barrier
     uint64_t trace_cap;
+    // resuming a paused peel (r0 > 0): the state words in st are the pause's,
+    // S0/E0/best the pause's values, and the first round scans every vertex,
+    // skipping those already failed; max_rounds > 0 pauses after that many rounds
+    uint64_t r0, S0, E0, best_round0, best_E0, best_V0;
+    uint64_t max_rounds;
 };
 
 // floor(2(p+q)E / (qS)) clamped to 32 bits; S > 0.
@@ -97,12 +103,14 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
     __shared__ PeelSmem<TB> sm;
     PeelCtl* ctl = a.ctl;
     const uint32_t tid = threadIdx.x;
-    uint64_t S = a.n, E = a.m;
-    uint64_t r = 0;
+    const bool resume = a.r0 > 0;
+    uint64_t S = resume ? a.S0 : a.n, E = resume ? a.E0 : a.m;
+    uint64_t r = a.r0;
     uint64_t short_lo = 0, chunk_lo = 0, surv_base = 0;
-    const uint32_t* alive = nullptr;  // round 0: identity
+    const uint32_t* alive = nullptr;  // first round: identity (a fresh peel) or every vertex (a resumed one)
     uint32_t* next = a.listA;
-    uint64_t best_E = E, best_V = S, best_round = 0;
+    uint64_t best_E = resume ? a.best_E0 : E, best_V = resume ? a.best_V0 : S;
+    uint64_t best_round = resume ? a.best_round0 : 0;
     uint64_t nstamp = 0;
     auto stamp = [&]() {
         if (a.trace && blockIdx.x == 0 && tid == 0 && nstamp < a.trace_cap) a.trace[nstamp] = global_ns();
@@ -111,7 +119,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
     stamp();
     agg_clear(sm.agg);
     const uint32_t hot = hot_threshold(a.hot_deg);
-    if (blockIdx.x == 0 && tid == 0) {
+    if (blockIdx.x == 0 && tid == 0 && !resume) {
         a.hist_S[0] = S;
         a.hist_E[0] = E;
     }
@@ -119,27 +127,36 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         const uint32_t T = peel_threshold(a.p, a.q, E, S);
         const uint32_t mark = kDead | (uint32_t)(r + 1);
         // ------------------------------------------------ phase 1: test + compact
-        for (uint64_t t = (uint64_t)blockIdx.x * TB; t < S; t += (uint64_t)gridDim.x * TB) {
+        const bool fresh = r == 0;                  // identity list, degrees from the rows
+        const bool scan_all = !alive && resume;     // a resumed peel's first round: every vertex, failed ones skipped
+        const uint64_t span = scan_all ? a.n : S;
+        for (uint64_t t = (uint64_t)blockIdx.x * TB; t < span; t += (uint64_t)gridDim.x * TB) {
             uint64_t i = t + tid;
-            bool valid = i < S;
+            bool valid = i < span;
             uint32_t v = 0, d = 0, nch = 0;
             uint64_t len = 0;
             bool fail = false;
             if (valid) {
-                if (r == 0) {
+                if (fresh) {
                     v = (uint32_t)i;
                     len = a.off[v + 1] - a.off[v];
                     d = (uint32_t)len;
+                } else if (scan_all) {
+                    v = (uint32_t)i;
+                    d = a.st[v];
+                    valid = !(d & kDead);
                 } else {
                     v = alive[i];
                     d = a.st[v];
                 }
+            }
+            if (valid) {
                 fail = d <= T;
                 if (fail) {
-                    if (r != 0) len = a.off[v + 1] - a.off[v];
+                    if (!fresh) len = a.off[v + 1] - a.off[v];
                     a.st[v] = mark;
                     if (len > a.short_max) nch = (uint32_t)((len + a.chunk_len - 1) / a.chunk_len);
-                } else if (r == 0) {
+                } else if (fresh) {
                     a.st[v] = d;
                 }
             }
@@ -239,6 +256,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         S = S1;
         E = E1;
         if (r >= a.hist_cap) break;
+        if (a.max_rounds && r - a.r0 >= a.max_rounds) break;  // pause: the state stays in st
     }
     if (blockIdx.x == 0 && tid == 0) {
         ctl->stamps = nstamp;
@@ -246,6 +264,8 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         ctl->best_round = best_round;
         ctl->best_E = best_E;
         ctl->best_V = best_V;
+        ctl->cur_S = S;
+        ctl->cur_E = E;
     }
 }
 
@@ -319,6 +339,7 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
     a.hot_deg = tu.hot_deg;
     a.trace = trace_dev;
     a.trace_cap = trace_cap;
+    a.r0 = a.S0 = a.E0 = a.best_round0 = a.best_E0 = a.best_V0 = a.max_rounds = 0;
     DSG_TRY_CUDA(sc.get(&a.st, n));
     DSG_TRY_CUDA(sc.get(&a.listA, n));
     DSG_TRY_CUDA(sc.get(&a.listB, n));
@@ -691,6 +712,7 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     a.hot_deg = tu.hot_deg;
     a.trace = nullptr;
     a.trace_cap = 0;
+    a.r0 = a.S0 = a.E0 = a.best_round0 = a.best_E0 = a.best_V0 = a.max_rounds = 0;
     // The buffer keeps whatever the previous call left; only the control
     // block must start at zero (every other array is written before it is read).
     DSG_TRY_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(PeelCtl), s));
@@ -719,3 +741,302 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     if (out_V) *out_V = c.best_V;
     return DSG_OK;
 }
+
+// ========================================================= snapshot / resume
+//
+// Algorithm 1's state between two rounds is small: each vertex's state word
+// (its degree inside S_r, or the round it failed in), the round r, |S_r|,
+// |E(S_r)|, the best round so far with its (E, V), and the history of
+// (|S_t|, |E(S_t)|).  A paused peel keeps that state on the device between
+// launches; a snapshot writes it to host memory, and resuming rebuilds it on
+// a handle of the same graph, so a long peel (eps = 0 on a graph that peels
+// slowly) can be checkpointed, moved or continued later with the same result.
+struct dsg_peel_state {
+    const dsg_graph* g = nullptr;
+    uint32_t p = 0, q = 1;
+    uint64_t r = 0, S = 0, E = 0, best_round = 0, best_E = 0, best_V = 0, cap = 0, chunk_cap = 0;
+    bool done = false;
+    dsg::Tuning tu;
+    uint32_t *st = nullptr, *listA = nullptr, *listB = nullptr, *F = nullptr;
+    uint64_t *C = nullptr, *hist_S = nullptr, *hist_E = nullptr;
+    dsg::PeelCtl* ctl = nullptr;
+};
+
+namespace dsg {
+
+static constexpr uint64_t kSnapMagic = 0x314c454550475344ull;  // "DSGPEEL1"
+static constexpr uint64_t kSnapHeaderWords = 16;
+
+static void peel_state_release(dsg_peel_state* ps) {
+    if (!ps) return;
+    cudaStream_t s = ps->g ? ps->g->stream : nullptr;
+    void* bufs[] = {ps->st, ps->listA, ps->listB, ps->F, ps->C, ps->hist_S, ps->hist_E, ps->ctl};
+    for (void* b : bufs)
+        if (b) dev_free(b, s);
+    if (s) cudaStreamSynchronize(s);
+    delete ps;
+}
+
+// A new state on g (device arrays allocated, scalars at round 0).
+static dsg_status peel_state_new(const dsg_graph* g, uint32_t p, uint32_t q, dsg_peel_state** out) {
+    dsg_peel_state* ps = new dsg_peel_state();
+    ps->g = g;
+    ps->p = p;
+    ps->q = q;
+    ps->tu = tuning_for(g, 0);
+    if (g->force_block) ps->tu.block = g->force_block;
+    const uint32_t n = g->n;
+    ps->cap = n ? dsg_round_bound(n, p, q) + 1 : 1;
+    ps->chunk_cap = (uint64_t)n + (2 * g->m) / ps->tu.chunk_len + 1;
+    ps->S = n;
+    ps->E = g->m;
+    ps->best_E = g->m;
+    ps->best_V = n;
+    ps->done = n == 0;
+    cudaStream_t s = g->stream;
+    const size_t nb = ((size_t)(n ? n : 1) * 4 + 255) & ~size_t(255);
+    cudaError_t e = dev_alloc((void**)&ps->st, nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->listA, nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->listB, nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->F, nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->C, ps->chunk_cap * 8, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->hist_S, ps->cap * 8, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->hist_E, ps->cap * 8, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->ctl, sizeof(PeelCtl), s);
+    if (e != cudaSuccess) {
+        set_error("peel state: %s", cudaGetErrorString(e));
+        peel_state_release(ps);
+        return e == cudaErrorMemoryAllocation ? DSG_ENOMEM : DSG_ECUDA;
+    }
+    *out = ps;
+    return DSG_OK;
+}
+
+// Run up to max_rounds rounds (0: to the end) from where ps stands.
+static dsg_status peel_state_run(dsg_peel_state* ps, uint64_t max_rounds) {
+    if (ps->done) return DSG_OK;
+    const dsg_graph* g = ps->g;
+    cudaStream_t s = g->stream;
+    PeelArgs a;
+    a.n = g->n;
+    a.m = g->m;
+    a.p = ps->p;
+    a.q = ps->q;
+    a.off = g->off;
+    a.adj = g->adj;
+    a.st = ps->st;
+    a.listA = ps->listA;
+    a.listB = ps->listB;
+    a.F = ps->F;
+    a.C = ps->C;
+    a.hist_S = ps->hist_S;
+    a.hist_E = ps->hist_E;
+    a.hist_cap = ps->cap;
+    a.ctl = ps->ctl;
+    a.limit_ns = wait_limit_ns();
+    a.short_max = ps->tu.short_max;
+    a.chunk_len = ps->tu.chunk_len;
+    a.hot_deg = ps->tu.hot_deg;
+    a.trace = nullptr;
+    a.trace_cap = 0;
+    a.r0 = ps->r;
+    a.S0 = ps->S;
+    a.E0 = ps->E;
+    a.best_round0 = ps->best_round;
+    a.best_E0 = ps->best_E;
+    a.best_V0 = ps->best_V;
+    a.max_rounds = max_rounds;
+    PeelCtl init;
+    memset(&init, 0, sizeof(init));
+    init.failed = (uint64_t)g->n - ps->S;  // the counters the kernel derives S and E from
+    init.dE = g->m - ps->E;
+    DSG_TRY_CUDA(cudaMemcpyAsync(ps->ctl, &init, sizeof(PeelCtl), cudaMemcpyHostToDevice, s));
+    cudaError_t e;
+    switch (ps->tu.block) {
+        case 256: e = launch_peel<256>(a, ps->tu.blocks_per_sm, s, g->max_blocks); break;
+        case 1024: e = launch_peel<1024>(a, ps->tu.blocks_per_sm, s, g->max_blocks); break;
+        default: e = launch_peel<512>(a, ps->tu.blocks_per_sm, s, g->max_blocks); break;
+    }
+    DSG_TRY_CUDA(e);
+    PeelCtl c;
+    DSG_TRY_CUDA(cudaMemcpyAsync(&c, ps->ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s));
+    DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    dsg_status st = status_from_err(c.err, "peel");
+    if (st != DSG_OK) return st;
+    ps->r = c.rounds;
+    ps->S = c.cur_S;
+    ps->E = c.cur_E;
+    ps->best_round = c.best_round;
+    ps->best_E = c.best_E;
+    ps->best_V = c.best_V;
+    ps->done = ps->S == 0;
+    return DSG_OK;
+}
+
+static uint64_t snapshot_bytes(const dsg_peel_state* ps) {
+    return (kSnapHeaderWords + 2 * (ps->r + 1)) * 8 + (uint64_t)ps->g->n * 4;
+}
+
+}  // namespace dsg
+
+extern "C" {
+
+dsg_status dsg_peel_begin(const dsg_graph* g, uint32_t eps_num, uint32_t eps_den, dsg_peel_state** out) {
+    clear_error();
+    DSG_CHECK_ARG(g && out, "graph / out is NULL");
+    DSG_CHECK_ARG(eps_den != 0, "eps_den must be positive");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    dsg_peel_state* ps = nullptr;
+    dsg_status st = peel_state_new(g, eps_num, eps_den, &ps);
+    if (st != DSG_OK) return st;
+    const uint64_t h[2] = {g->n, g->m};
+    cudaError_t e = cudaMemcpyAsync(ps->hist_S, &h[0], 8, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ps->hist_E, &h[1], 8, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        set_error("peel_begin: %s", cudaGetErrorString(e));
+        peel_state_release(ps);
+        return DSG_ECUDA;
+    }
+    *out = ps;
+    return DSG_OK;
+}
+
+dsg_status dsg_peel_advance(dsg_peel_state* ps, uint32_t max_rounds, uint64_t* rounds, uint32_t* done) {
+    clear_error();
+    DSG_CHECK_ARG(ps, "state is NULL");
+    DSG_TRY_CUDA(cudaSetDevice(ps->g->device));
+    dsg_status st = peel_state_run(ps, max_rounds);
+    if (st != DSG_OK) return st;
+    if (rounds) *rounds = ps->r;
+    if (done) *done = ps->done ? 1u : 0u;
+    return DSG_OK;
+}
+
+dsg_status dsg_peel_snapshot_size(const dsg_peel_state* ps, uint64_t* bytes) {
+    clear_error();
+    DSG_CHECK_ARG(ps && bytes, "state / bytes is NULL");
+    *bytes = snapshot_bytes(ps);
+    return DSG_OK;
+}
+
+dsg_status dsg_peel_snapshot(const dsg_peel_state* ps, void* buf, uint64_t bytes) {
+    clear_error();
+    DSG_CHECK_ARG(ps && buf, "state / buffer is NULL");
+    DSG_CHECK_ARG(bytes >= snapshot_bytes(ps), "buffer smaller than dsg_peel_snapshot_size");
+    DSG_TRY_CUDA(cudaSetDevice(ps->g->device));
+    uint64_t* w = static_cast<uint64_t*>(buf);
+    const uint64_t hl = ps->r + 1;
+    const uint64_t h[kSnapHeaderWords] = {kSnapMagic, 1, ps->g->n, ps->g->m, ps->p, ps->q, ps->r, ps->S, ps->E,
+                                          ps->best_round, ps->best_E, ps->best_V, hl, 0, 0, 0};
+    memcpy(w, h, sizeof(h));
+    cudaStream_t s = ps->g->stream;
+    DSG_TRY_CUDA(copy_any(w + kSnapHeaderWords, ps->hist_S, hl * 8, s));
+    DSG_TRY_CUDA(copy_any(w + kSnapHeaderWords + hl, ps->hist_E, hl * 8, s));
+    uint32_t* words = reinterpret_cast<uint32_t*>(w + kSnapHeaderWords + 2 * hl);
+    if (ps->r > 0) {
+        if (ps->g->n) DSG_TRY_CUDA(copy_any(words, ps->st, (size_t)ps->g->n * 4, s));
+    } else {
+        memset(words, 0, (size_t)ps->g->n * 4);  // before the first round the state words are not used
+    }
+    DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    return DSG_OK;
+}
+
+dsg_status dsg_peel_resume(const dsg_graph* g, const void* buf, uint64_t bytes, dsg_peel_state** out) {
+    clear_error();
+    DSG_CHECK_ARG(g && buf && out, "graph / buffer / out is NULL");
+    DSG_CHECK_ARG(bytes >= kSnapHeaderWords * 8, "buffer shorter than a snapshot header");
+    const uint64_t* w = static_cast<const uint64_t*>(buf);
+    DSG_CHECK_ARG(w[0] == kSnapMagic && w[1] == 1, "not a peel snapshot (magic / version)");
+    DSG_CHECK_ARG(w[2] == g->n && w[3] == g->m, "the snapshot was taken on a graph of another size");
+    DSG_CHECK_ARG(w[5] != 0 && w[4] <= 0xffffffffull && w[5] <= 0xffffffffull, "bad eps in the snapshot");
+    const uint64_t r = w[6], hl = w[12];
+    DSG_CHECK_ARG(hl == r + 1, "bad history length in the snapshot");
+    DSG_CHECK_ARG(bytes >= (kSnapHeaderWords + 2 * hl) * 8 + (uint64_t)g->n * 4, "snapshot truncated");
+    DSG_CHECK_ARG(w[7] <= g->n && w[8] <= g->m && w[9] <= r && w[11] <= g->n, "inconsistent snapshot scalars");
+    DSG_TRY_CUDA(cudaSetDevice(g->device));
+    dsg_peel_state* ps = nullptr;
+    dsg_status st = peel_state_new(g, (uint32_t)w[4], (uint32_t)w[5], &ps);
+    if (st != DSG_OK) return st;
+    if (hl > ps->cap) {
+        set_error("peel_resume: the snapshot has %llu rounds, more than the bound %llu for its eps",
+                  (unsigned long long)r, (unsigned long long)(ps->cap - 1));
+        peel_state_release(ps);
+        return DSG_EINVAL;
+    }
+    ps->r = r;
+    ps->S = w[7];
+    ps->E = w[8];
+    ps->best_round = w[9];
+    ps->best_E = w[10];
+    ps->best_V = w[11];
+    ps->done = ps->S == 0;
+    cudaStream_t s = g->stream;
+    cudaError_t e = copy_any(ps->hist_S, w + kSnapHeaderWords, hl * 8, s);
+    if (e == cudaSuccess) e = copy_any(ps->hist_E, w + kSnapHeaderWords + hl, hl * 8, s);
+    if (e == cudaSuccess && r > 0 && g->n)
+        e = copy_any(ps->st, reinterpret_cast<const uint32_t*>(w + kSnapHeaderWords + 2 * hl), (size_t)g->n * 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error("peel_resume: %s", cudaGetErrorString(e));
+        peel_state_release(ps);
+        return DSG_ECUDA;
+    }
+    *out = ps;
+    return DSG_OK;
+}
+
+dsg_status dsg_peel_finish(dsg_peel_state* ps, uint8_t* out_set, uint64_t* out_E, uint64_t* out_V,
+                           uint64_t* out_rounds, uint64_t* hist_S, uint64_t* hist_E, uint64_t hist_cap) {
+    clear_error();
+    DSG_CHECK_ARG(ps, "state is NULL");
+    DSG_TRY_CUDA(cudaSetDevice(ps->g->device));
+    dsg_status st = peel_state_run(ps, 0);
+    if (st != DSG_OK) return st;
+    const dsg_graph* g = ps->g;
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    if (out_set && n) {
+        Scratch sc(s);
+        uint8_t* set_dev = out_set;
+        const bool direct = is_device_ptr(out_set);
+        if (!direct) DSG_TRY_CUDA(sc.get(&set_dev, n));
+        PeelCtl c;
+        memset(&c, 0, sizeof(c));
+        c.best_round = ps->best_round;
+        DSG_TRY_CUDA(cudaMemcpyAsync(ps->ctl, &c, sizeof(PeelCtl), cudaMemcpyHostToDevice, s));
+        uint64_t want = ((uint64_t)n + 255) / 256, cap_b = (uint64_t)dev_info().sms * 8;
+        {
+            LaunchScope ls("peel_finish", s);
+            peel_finish_kernel<<<(uint32_t)(want < cap_b ? want : cap_b), 256, 0, s>>>(n, ps->st, ps->ctl, nullptr,
+                                                                                       set_dev);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+        if (!direct) DSG_TRY_CUDA(copy_any(out_set, set_dev, n, s));
+        DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    const uint64_t R = ps->r;
+    if (hist_S || hist_E) {
+        const uint64_t k = R + 1 < hist_cap ? R + 1 : hist_cap;
+        if (hist_S && k) DSG_TRY_CUDA(copy_any(hist_S, ps->hist_S, k * 8, s));
+        if (hist_E && k) DSG_TRY_CUDA(copy_any(hist_E, ps->hist_E, k * 8, s));
+        DSG_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    if (out_E) *out_E = n ? ps->best_E : 0;
+    if (out_V) *out_V = n ? ps->best_V : 0;
+    if (out_rounds) *out_rounds = R;
+    if ((hist_S || hist_E) && hist_cap < R + 1) {
+        set_error("peel_finish: history needs %llu slots, got %llu", (unsigned long long)(R + 1),
+                  (unsigned long long)hist_cap);
+        return DSG_EOVERFLOW;
+    }
+    return DSG_OK;
+}
+
+void dsg_peel_free(dsg_peel_state* ps) {
+    if (ps && ps->g) cudaSetDevice(ps->g->device);
+    peel_state_release(ps);
+}
+
+}  // extern "C"

@@ -80,10 +80,11 @@ struct dsg_server {
 
 namespace dsg {
 
-// device bytes a request may hold while resident: raw pairs during ingest,
-// ingest temporaries, the CSR and the batch scratch
+// device bytes a request may hold while resident: raw pairs during ingest
+// (8 per pair), ingest temporaries (two bucket passes of 16 per pair, the
+// unsorted rows 8 per pair, per-vertex arrays), the CSR and the batch scratch
 static size_t request_charge(uint32_t n, uint64_t m_raw) {
-    return (size_t)m_raw * 8 * 4 + (size_t)n * 64 + 4096;
+    return (size_t)m_raw * 64 + (size_t)n * 96 + (64u << 10);
 }
 
 struct Inflight {

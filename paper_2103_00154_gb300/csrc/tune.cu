@@ -33,6 +33,9 @@ Tuning current_tuning() {
         t.local_max = env_u32("DSG_LOCAL_MAX", t.local_max);
         t.local_work = env_u32("DSG_LOCAL_WORK", t.local_work);
         t.inline_max = env_u32("DSG_INLINE_MAX", t.inline_max);
+        t.tail_max = env_u32("DSG_KCORE_TAIL", t.tail_max);
+        t.batch_split = env_u32("DSG_BATCH_SPLIT", t.batch_split);
+        if (t.tail_max > kTailMaxVertices) t.tail_max = kTailMaxVertices;
         if (t.block != 256 && t.block != 512 && t.block != 1024) t.block = 512;
         if (t.chunk_len < 32) t.chunk_len = 32;
         if (t.short_max < 1) t.short_max = 1;
@@ -82,6 +85,23 @@ extern "C" dsg_status dsg_set_inline_max(uint32_t inline_max) {
     current_tuning();
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.inline_max = inline_max;
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_set_kcore_tail(uint32_t max_vertices) {
+    clear_error();
+    DSG_CHECK_ARG(max_vertices <= kTailMaxVertices, "max_vertices must be at most 131072");
+    current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.tail_max = max_vertices;
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_set_batch_split(uint32_t min_work) {
+    clear_error();
+    current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.batch_split = min_work;
     return DSG_OK;
 }
 
@@ -174,6 +194,8 @@ static int load_table_locked(const char* path) {
         parse_u32(obj.c_str(), "local_max", &t.local_max);
         parse_u32(obj.c_str(), "local_work", &t.local_work);
         parse_u32(obj.c_str(), "inline_max", &t.inline_max);
+        parse_u32(obj.c_str(), "kcore_tail", &t.tail_max);
+        if (t.tail_max > kTailMaxVertices) t.tail_max = kTailMaxVertices;
         if ((t.block == 256 || t.block == 512 || t.block == 1024) && t.chunk_len >= 32 && t.short_max >= 1) {
             g_table[key] = t;
             ++loaded;
@@ -279,12 +301,14 @@ extern "C" dsg_status dsg_autotune(const dsg_graph* g, uint32_t eps_num, uint32_
                                    {&Tuning::chunk_len, {128, 256, 1024}, 3},
                                    {&Tuning::short_max, {16, 32, 64}, 3}};
         const Knob core_knobs[] = {{&Tuning::block, {256, 512, 1024}, 3},
+                                   {&Tuning::blocks_per_sm, {0, 1}, 2},
                                    {&Tuning::local_max, {256, 1024, 4096}, 3},
                                    {&Tuning::local_work, {4096, 16384, 65536}, 3},
                                    {&Tuning::inline_max, {256, 1024, 4096, 16384}, 4},
-                                   {&Tuning::chunk_len, {256, 1024, 2048}, 3}};
+                                   {&Tuning::chunk_len, {256, 1024, 2048}, 3},
+                                   {&Tuning::tail_max, {0, 16384, 32768, 131072}, 4}};
         const Knob* knobs = kernel == 0 ? peel_knobs : core_knobs;
-        const int nknobs = kernel == 0 ? 4 : 5;
+        const int nknobs = kernel == 0 ? 4 : 7;
         for (int kk = 0; kk < nknobs; ++kk) {
             for (int vi = 0; vi < knobs[kk].count; ++vi) {
                 Tuning cand = best;
@@ -330,9 +354,10 @@ extern "C" dsg_status dsg_tune_save(const char* path) {
         auto ms = g_table_ms.find(kv.first);
         fprintf(f,
                 "  {\"key\": \"%s\", \"block\": %u, \"blocks_per_sm\": %u, \"short_max\": %u, \"chunk_len\": %u, "
-                "\"hot_deg\": %u, \"local_max\": %u, \"local_work\": %u, \"inline_max\": %u, \"ms\": %.4f}%s\n",
+                "\"hot_deg\": %u, \"local_max\": %u, \"local_work\": %u, \"inline_max\": %u, \"kcore_tail\": %u, "
+                "\"ms\": %.4f}%s\n",
                 kv.first.c_str(), t.block, t.blocks_per_sm, t.short_max, t.chunk_len, t.hot_deg, t.local_max,
-                t.local_work, t.inline_max, ms == g_table_ms.end() ? -1.0 : ms->second,
+                t.local_work, t.inline_max, t.tail_max, ms == g_table_ms.end() ? -1.0 : ms->second,
                 ++i < g_table.size() ? "," : "");
     }
     fprintf(f, "]}\n");
@@ -370,13 +395,13 @@ extern "C" uint32_t dsg_tune_entries(void) {
     return (uint32_t)g_table.size();
 }
 
-extern "C" dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[8]) {
+extern "C" dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint32_t out[9]) {
     clear_error();
     DSG_CHECK_ARG(g && out, "graph or out is NULL");
     DSG_CHECK_ARG(kernel <= 1, "kernel must be 0 (peel) or 1 (core numbers)");
     const Tuning t = tuning_for(g, (int)kernel);
-    const uint32_t v[8] = {t.block,     t.blocks_per_sm, t.short_max,  t.chunk_len,
-                           t.hot_deg,   t.local_max,     t.local_work, t.inline_max};
+    const uint32_t v[9] = {t.block,   t.blocks_per_sm, t.short_max,  t.chunk_len, t.hot_deg,
+                           t.local_max, t.local_work,  t.inline_max, t.tail_max};
     memcpy(out, v, sizeof(v));
     return DSG_OK;
 }

@@ -86,3 +86,34 @@ def test_method_decrements_are_degree_minus_core():
         m = sum(len(r) for r in rows) // 2
         core, dec = _serial_level_peel_decrements(n, rows)
         assert dec == bench.kcore_pkc_atomics(m, int(np.sum(core)))
+
+
+def test_replica_launch_command_starts_n_ranks_on_localhost():
+    cmd = bench.replica_launch_cmd(["--gpus", "4", "--steps", "2"], 4, 29501)
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "--master-addr=127.0.0.1" in cmd and "--master-port=29501" in cmd
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "2"]
+    assert cmd[cmd.index("--master-port=29501") + 1].endswith("bench.py")
+
+
+def test_replica_launch_runs_ranks_that_see_the_world(tmp_path):
+    """The launcher command, pointed at a probe script instead of bench.py,
+    starts two gloo ranks on CPU that agree on the world size."""
+    import subprocess
+    import sys
+    probe = tmp_path / "probe.py"
+    probe.write_text("import os, torch.distributed as d\n"
+                     "d.init_process_group('gloo')\n"
+                     "print('rank', d.get_rank(), 'of', d.get_world_size(), flush=True)\n"
+                     "d.destroy_process_group()\n")
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = bench.replica_launch_cmd([], 2, port)
+    at = [i for i, c in enumerate(cmd) if c.endswith("bench.py")]
+    assert len(at) == 1
+    cmd[at[0]] = str(probe)
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=240)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert "rank 0 of 2" in out.stdout and "rank 1 of 2" in out.stdout

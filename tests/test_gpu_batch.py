@@ -103,3 +103,36 @@ def test_batch_with_graphs_above_the_block_share():
         lo, hi = int(vbh[g]), int(vbh[g + 1])
         np.testing.assert_array_equal(out_set[lo:hi].cpu().numpy(), want.mask)
         np.testing.assert_array_equal(core[lo:hi].cpu().numpy().view(np.uint32), oracle.kcore_bz(c))
+
+
+@pytest.mark.parametrize("split", ["auto", "block_per_graph"])
+def test_full_size_batch_members_match_the_oracle(split):
+    """Members of the 4,096-graph batch workload at their full sizes -- the
+    largest of them (n ~ 10^6) and a seeded sample -- solved together, with
+    the default split (the largest go to the grid-wide kernels) and with every
+    graph in the block-per-graph launch, as in the full batch: mask, (E, V),
+    R, best round and core numbers against the oracle."""
+    ns = np.array([inputs.batch_n(i) for i in range(4096)])
+    rng = np.random.default_rng(2024)
+    members = sorted({int(ns.argmax()), int(ns.argmin())} | set(int(x) for x in rng.choice(4096, 4, replace=False)))
+    raws = [inputs.batch_graph(i) for i in members]
+    csrs = [oracle.from_raw(r) for r in raws]
+    vb, off, adj = dsg.pack_batch([(c.off, c.adj) for c in csrs], device="cuda")
+    dsg.set_tuning(batch_split=0 if split == "auto" else 0xffffffff)
+    try:
+        solver = dsg.BatchSolver(vb, off, adj, [(1, 10)], np.ones(len(raws), np.uint8))
+        N = solver.N
+        out_set = torch.zeros(N, dtype=torch.uint8, device="cuda")
+        core = torch.zeros(N, dtype=torch.int32, device="cuda")
+        E, V, R, BR = solver.solve(out_set=out_set, core=core)
+    finally:
+        dsg.set_tuning()
+    vbh = vb.cpu().numpy().view(np.uint64)
+    for g, c in enumerate(csrs):
+        want = oracle.bahmani(c, 1, 10)
+        assert (int(E[g]), int(V[g]), int(R[g]), int(BR[g])) == (want.E, want.V, want.rounds, want.best_round), \
+            members[g]
+        lo, hi = int(vbh[g]), int(vbh[g + 1])
+        np.testing.assert_array_equal(out_set[lo:hi].cpu().numpy(), want.mask, err_msg=str(members[g]))
+        np.testing.assert_array_equal(core[lo:hi].cpu().numpy().view(np.uint32), oracle.kcore_bz(c),
+                                      err_msg=str(members[g]))

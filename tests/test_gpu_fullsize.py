@@ -3,15 +3,14 @@ times (library defaults).
 
 * R-MAT scale 20 (the bench workload): every output against the oracle,
   element by element (the oracle needs a few seconds here).
-* Chung-Lu 2^24 / 2^28 pairs: the CSR on sampled rows rebuilt from the raw
-  pairs, the peel's history against invariants that hold at any size
-  (|S_r| from the failure rounds, 2|E(S_r)| recounted from the CSR, the
-  kept set's induced edge count), and core numbers against the k-core
-  properties on all vertices.  With DSG_FULL_ORACLE=1 the oracle also runs
-  on the whole graph (minutes of CPU).
+* Chung-Lu 2^24 / 2^28 pairs (the largest single-graph workload): every
+  output against the oracle run on the whole graph (about two minutes of
+  serial CPU), after the checks that need no oracle: the CSR on sampled
+  rows rebuilt from the raw pairs, the peel's history against invariants
+  that hold at any size (|S_r| from the failure rounds, 2|E(S_r)| recounted
+  from the CSR, the kept set's induced edge count, the best round the
+  earliest strict argmax), and core numbers against the k-core properties.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -93,6 +92,15 @@ def _check_peel_properties(off, adj, tr, p, q):
     sel = tr.mask.astype(bool)
     assert int(sel.sum()) == tr.V
     assert int(np.count_nonzero(sel[src] & sel[adj])) == 2 * tr.E
+    # the kept set is S_b for the earliest b maximising |E(S_r)| / |S_r| over the non-empty S_r
+    b = tr.best_round
+    assert 0 <= b < R and (hS[b], hE[b]) == (tr.V, tr.E)
+    live = hS[:R] > 0
+    assert live.all()
+    lhs = hE[:R].astype(object) * int(hS[b])
+    rhs = int(hE[b]) * hS[:R].astype(object)
+    assert all(l <= r for l, r in zip(lhs, rhs))          # no round denser than b
+    assert all(l < r for l, r in zip(lhs[:b], rhs[:b]))   # every earlier round strictly sparser
 
 
 def _check_core_properties(off, adj, core):
@@ -110,9 +118,12 @@ def _check_core_properties(off, adj, core):
     assert (ge1 < core + 1).all()
 
 
-def test_chung_lu_2_24_properties_and_sampled_rows():
+def test_chung_lu_2_24_all_outputs_bit_exact():
     raw = inputs.chung_lu(n=1 << 24, m_draws=1 << 28, gamma=2.1, mean=32.0, wmax=1e5, seed=2)
     g = _device_graph(raw)
+    # the launch parameters bench.py times: autotuned for this graph's size class
+    dsg.tune_clear()
+    g.autotune(1, 10)
     off, adj = g.csr()
     n = raw.n
     # sampled rows rebuilt from the raw pairs, one by one
@@ -132,11 +143,19 @@ def test_chung_lu_2_24_properties_and_sampled_rows():
     _check_peel_properties(off, adj, tr, 1, 10)
     core = g.kcore()
     _check_core_properties(off, adj, core)
-    if os.environ.get("DSG_FULL_ORACLE") == "1":
-        c = oracle.canonical_csr(n, raw.src, raw.dst)
-        np.testing.assert_array_equal(off, c.off)
-        np.testing.assert_array_equal(adj, c.adj)
-        want = oracle.bahmani(c, 1, 10)
-        assert (tr.rounds, tr.best_round, tr.E, tr.V) == (want.rounds, want.best_round, want.E, want.V)
-        np.testing.assert_array_equal(tr.peel_round, want.peel_round)
-        np.testing.assert_array_equal(core, oracle.kcore_bz(c))
+    g.close()
+    dsg.tune_clear()
+    del g
+    # the whole graph through the oracle: CSR bytes, every peel output, core numbers
+    c = oracle.canonical_csr(n, raw.src, raw.dst)
+    del raw
+    np.testing.assert_array_equal(off, c.off)
+    np.testing.assert_array_equal(adj, c.adj)
+    del off, adj
+    want = oracle.bahmani(c, 1, 10)
+    assert (tr.rounds, tr.best_round, tr.E, tr.V) == (want.rounds, want.best_round, want.E, want.V)
+    np.testing.assert_array_equal(tr.hist_S, want.hist_S)
+    np.testing.assert_array_equal(tr.hist_E, want.hist_E)
+    np.testing.assert_array_equal(tr.peel_round, want.peel_round)
+    np.testing.assert_array_equal(tr.mask, want.mask)
+    np.testing.assert_array_equal(core, oracle.kcore_bz(c))

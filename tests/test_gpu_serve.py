@@ -136,3 +136,43 @@ def test_shutdown_with_requests_in_flight():
     _, E, V = gr.bahmani(1, 10)
     want = oracle.bahmani(c, 1, 10)
     assert (E, V) == (want.E, want.V)
+
+
+def test_full_size_pool_requests_match_the_oracle_with_sets_and_cores():
+    """Requests drawn as in the serving workload (pool graphs of n up to
+    2,000,000, seeds 7,000,000 + i; eps 1/100 or 1/10; core numbers on half of
+    them), including the largest pool member of the first 256, submitted as a
+    burst: every result -- (E, V), rounds, best round, the set and the core
+    numbers when asked -- equals the oracle's for that (graph, eps)."""
+    ns = np.array([inputs.batch_n(i, seed_base=7_000_000, n_hi=2_000_000) for i in range(256)])
+    rng = np.random.default_rng(7)
+    picks = sorted({int(ns.argmax())} | set(int(x) for x in rng.choice(256, 5, replace=False)))
+    pool = {i: inputs.batch_graph(i, seed_base=7_000_000, n_hi=2_000_000) for i in picks}
+    csrs = {i: oracle.from_raw(g) for i, g in pool.items()}
+    cache = {}
+    with dsg.Server(max_batch=8) as srv:
+        tickets = []
+        for r in range(12):
+            i = picks[r % len(picks)]
+            p, q = [(1, 100), (1, 10)][int(rng.integers(2))]
+            want_core = bool(rng.random() < 0.5)
+            g = pool[i]
+            out_set = np.zeros(max(g.n, 1), np.uint8)
+            core = np.zeros(max(g.n, 1), np.uint32) if want_core else None
+            t = srv.submit(g.n, g.src, g.dst, p, q, want_core, out_set, core)
+            assert t is not None
+            tickets.append((t, i, p, q, out_set, core))
+        for t, i, p, q, out_set, core in tickets:
+            resp = srv.wait(t, timeout_s=120)
+            key = (i, p, q)
+            if key not in cache:
+                cache[key] = oracle.bahmani(csrs[i], p, q)
+            want = cache[key]
+            assert resp["status"] == 0
+            assert (resp["E"], resp["V"], resp["rounds"], resp["best_round"]) == \
+                (want.E, want.V, want.rounds, want.best_round)
+            np.testing.assert_array_equal(out_set[:csrs[i].n], want.mask)
+            if core is not None:
+                if ("core", i) not in cache:
+                    cache[("core", i)] = oracle.kcore_bz(csrs[i])
+                np.testing.assert_array_equal(core[:csrs[i].n], cache[("core", i)])

@@ -422,3 +422,25 @@ def test_chung_lu_weights_shape():
     w = inputs.chung_lu_weights(1 << 16, 2.1, 32.0, 1000.0)
     assert abs(w.mean() - 32.0) < 1e-6 * 32 and abs(w[0] - 1000.0) < 1e-6 * 1000
     assert (np.diff(w) <= 0).all()
+
+
+def test_table3_cbds_not_below_the_eps0_peel_on_synthetic_graphs():
+    """Table 3 (Sec. 4) reports CBDS-P's density at or above P-Bahmani's at
+    eps = 0 on every dataset.  The datasets are not available; the same
+    comparison, exact in rationals, on synthetic stand-ins of each family the
+    benchmarks use (planted-block Erdos-Renyi, R-MAT, Chung-Lu, batch members).
+    It is an observation of the paper, not a theorem; these instances hold it."""
+    from fractions import Fraction
+    cases = [inputs.er_block(n=3000, m=12000, k=40 + 5 * s, p=0.3 + 0.05 * (s % 5), seed=s) for s in range(6)]
+    cases += [inputs.rmat(scale=12 + s % 3, m=(8 + 4 * (s % 3)) << (12 + s % 3), seed=100 + s) for s in range(3)]
+    cases += [inputs.chung_lu(n=1 << 12, m_draws=1 << 16, gamma=2.1 + 0.1 * s, mean=16.0, wmax=0.0, seed=200 + s)
+              for s in range(3)]
+    cases += [inputs.batch_graph(i, n_lo=1000, n_hi=8000) for i in range(4)]
+    for raw in cases:
+        c = oracle.from_raw(raw)
+        peel0 = oracle.bahmani(c, 0, 1)
+        core = oracle.kcore_bz(c)
+        k, Ek, Vk = oracle.densest_core(c, core)
+        me, mv, _, _ = oracle.cbds_phase2(c, core, k, Ek, Vk)
+        assert Fraction(me, mv) >= Fraction(peel0.E, peel0.V), raw.name
+        assert Fraction(me, mv) >= Fraction(Ek, Vk), raw.name  # phase 2 never loses density (Sec. 3.2)
