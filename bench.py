@@ -121,7 +121,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs in the batch workload")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests per second")
-    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--serve-max-batch", type=int, default=256, help="serve: most graphs per batch launch")
     ap.add_argument("--pool", type=int, default=128, help="serve: distinct pre-generated graphs")
     return ap.parse_args()
 
@@ -574,8 +575,16 @@ def run_batch(args, wl, rank, world):
     out_set = torch.empty(max(Nv, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    tuning = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        trials = solver.autotune()
+        tuning = {"trials": trials, "seconds": round(time.perf_counter() - t0, 3)}
     for _ in range(max(args.warmup, 1)):
         E, V, R, BR = solver.solve(out_set=out_set, stream=stream)
+    # counters of the byte model, from one solve outside the timed region
+    bstats = np.zeros(4, np.uint64)
+    solver.solve(out_set=out_set, stream=stream, stats=bstats)
     torch.cuda.synchronize()
     L.dsg_profile_reset()
     L.dsg_profile_enable(1)
@@ -593,7 +602,20 @@ def run_batch(args, wl, rank, world):
             ms_steps.append(a_ev.elapsed_time(b_ev))
     launches = L.dsg_launch_count() - launches0
     L.dsg_profile_enable(0)
+    prof = N.profile_report()
     total_ms, value = aggregate_ranks(sum(ms_steps), G, args.steps, world, device=dev)
+    # roofline of the block-per-graph launch: the peel byte model summed over its graphs
+    roof = None
+    if "batch_solve" in prof and int(bstats[3]) == 0:
+        cnt, tot = prof["batch_solve"]
+        sum_S, dec, entries = int(bstats[0]), int(bstats[1]), int(bstats[2])
+        alg = peel_bytes(int(Nv), entries // 2, {"sum_S": sum_S, "decrements": dec})
+        peak, peak_kind = measured_peaks()
+        achieved = alg / (tot / cnt * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "batch_solve", "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "alg_bytes_per_launch": int(alg), "avg_launch_ms": round(tot / cnt, 4),
+                "model": "sum over the batch's graphs of the single-graph peel byte model"}
     # plain form: one dsg_bahmani per graph on the same resident graphs
     masks = [torch.empty(max(g.n, 1), dtype=torch.uint8, device=dev) for g in graphs]
     for g, m in zip(graphs[:64], masks[:64]):
@@ -607,21 +629,44 @@ def run_batch(args, wl, rank, world):
     return {"ms_per_step": total_ms / args.steps, "value": value, "edges": A, "N": Nv, "t_gen_s": t_gen,
             "t_ingest_s": t_ingest, "plain_ms": t_plain * 1e3, "plain_graphs_per_s": G / t_plain,
             "batched_equals_plain": bool(same), "gpu_launches": int(launches), "clocks": clk.summary(),
-            "rounds_max": int(R.max()), "raws": raws, "E": E, "V": V, "R": R, "BR": BR}
+            "rounds_max": int(R.max()), "raws": raws, "E": E, "V": V, "R": R, "BR": BR, "roofline": roof,
+            "tuning": tuning, "kernel_ms": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
+            "grid_path_graphs": int(bstats[3])}
+
+
+def _serve_oracle(n, src, dst, eps):
+    """Oracle results of one pool graph (runs in a worker process): per eps
+    (E, V, rounds, best round, set), and the core numbers."""
+    import oracle
+    c = oracle.canonical_csr(n, src, dst)
+    out = {}
+    for p, q in eps:
+        w = oracle.bahmani(c, p, q)
+        out[(p, q)] = (w.E, w.V, w.rounds, w.best_round, np.asarray(w.mask, np.uint8))
+    return out, np.asarray(oracle.kcore_bz(c), np.uint32)
 
 
 def run_serve(args, wl):
     """Poisson request stream against dsg_serve_*; pool graphs live in pinned
-    host memory and are lent to the server (no copy at submit)."""
+    host memory and are lent to the server (no copy at submit).  Every
+    completed request is checked against the oracle's result for its (pool
+    graph, eps): (E, V), rounds, best round, the set, and the core numbers when
+    asked."""
     import threading
+    import multiprocessing as mproc
     import torch
     import paper_2103_00154_gb300 as dsg
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
     from concurrent.futures import ThreadPoolExecutor
+    # the oracle cache first, in spawned processes (no CUDA context in this process yet)
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         pool = list(ex.map(lambda i: inputs.batch_graph(i, seed_base=7_000_000, n_hi=2_000_000, threads=1),
                            range(args.pool)))
+    t0 = time.perf_counter()
+    with mproc.get_context("spawn").Pool(os.cpu_count() or 1) as pp:
+        cache = pp.starmap(_serve_oracle, [(g.n, g.src, g.dst, wl["eps"]) for g in pool])
+    t_oracle = time.perf_counter() - t0
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
     pinned = [(torch.from_numpy(g.src.view(np.int32)).pin_memory(), torch.from_numpy(g.dst.view(np.int32)).pin_memory())
               for g in pool]
     rng = np.random.default_rng(7)
@@ -631,25 +676,25 @@ def run_serve(args, wl):
     eps_i = rng.integers(0, len(wl["eps"]), n_req)
     cores = rng.random(n_req) < 0.5
     # plain form first: one request at a time through the one-graph calls
-    plain_ref = {}
     t0 = time.perf_counter()
     n_plain = 0
     for i in range(min(n_req, 200)):
         g = pool[picks[i]]
         p, q = wl["eps"][eps_i[i]]
         gr = dsg.Graph.from_edges(g.n, pinned[picks[i]][0], pinned[picks[i]][1])
-        _, E, V = gr.bahmani(p, q, want_set=False)
+        gr.bahmani(p, q, want_set=False)
         if cores[i]:
             gr.kcore()
         gr.close()
-        plain_ref[(int(picks[i]), p, q)] = (E, V)
         n_plain += 1
     plain_gps = n_plain / (time.perf_counter() - t0)
-    srv = dsg.Server(max_batch=1024)
+    srv = dsg.Server(max_batch=args.serve_max_batch)
     tickets = [None] * n_req
+    bufs = [None] * n_req
     rejected = 0
     done = threading.Event()
-    results = {}
+    lat = []
+    check = {"checked": 0, "mismatch": 0, "sets": 0, "cores": 0, "bad_status": 0}
 
     def collector():
         i = 0
@@ -665,9 +710,23 @@ def run_serve(args, wl):
                 i += 1
                 continue
             r = srv.poll(t, 200_000)
-            if r is not None:
-                results[i] = r
-                i += 1
+            if r is None:
+                continue
+            lat.append(r["latency_us"])
+            out_set, core = bufs[i]
+            want, want_core = cache[int(picks[i])]
+            E, V, R, BR, mask = want[tuple(wl["eps"][eps_i[i]])]
+            ok = r["status"] == 0 and (r["E"], r["V"], r["rounds"], r["best_round"]) == (E, V, R, BR)
+            ok = ok and np.array_equal(out_set, mask)
+            check["sets"] += 1
+            if core is not None:
+                ok = ok and np.array_equal(core, want_core)
+                check["cores"] += 1
+            check["bad_status"] += r["status"] != 0
+            check["checked"] += 1
+            check["mismatch"] += not ok
+            bufs[i] = None
+            i += 1
 
     th = threading.Thread(target=collector)
     th.start()
@@ -678,9 +737,14 @@ def run_serve(args, wl):
             time.sleep(delay)
         g = pool[picks[i]]
         p, q = wl["eps"][eps_i[i]]
-        t = srv.submit(g.n, pinned[picks[i]][0], pinned[picks[i]][1], p, q, bool(cores[i]), borrow=True)
+        out_set = np.empty(max(g.n, 1), np.uint8)
+        core = np.empty(max(g.n, 1), np.uint32) if cores[i] else None
+        bufs[i] = (out_set[:g.n], None if core is None else core[:g.n])
+        t = srv.submit(g.n, pinned[picks[i]][0], pinned[picks[i]][1], p, q, bool(cores[i]), out_set, core,
+                       borrow=True)
         if t is None:
             rejected += 1
+            bufs[i] = None
             tickets[i] = -1
         else:
             tickets[i] = t
@@ -690,19 +754,15 @@ def run_serve(args, wl):
     wall = time.perf_counter() - start
     st = srv.stats()
     srv.close()
-    lat = np.array([r["latency_us"] for r in results.values()])
-    ok = all(r["status"] == 0 for r in results.values())
-    mismatch = 0
-    for i, r in results.items():
-        key = (int(picks[i]), *wl["eps"][eps_i[i]])
-        if key in plain_ref and plain_ref[key] != (r["E"], r["V"]):
-            mismatch += 1
-    completed = len(results)
+    lat = np.array(lat)
+    completed = len(lat)
     return {"completed": completed, "rejected": rejected, "offered": n_req, "offered_rate": n_req / offered_s,
-            "graphs_per_s": completed / wall, "wall_s": wall, "p50_us": float(np.percentile(lat, 50)) if completed else None,
+            "graphs_per_s": completed / wall, "wall_s": wall,
+            "p50_us": float(np.percentile(lat, 50)) if completed else None,
             "p99_us": float(np.percentile(lat, 99)) if completed else None, "batches": st["batches"],
-            "plain_graphs_per_s": plain_gps, "all_ok": ok, "mismatch_vs_plain": mismatch,
-            "checked_vs_plain": sum(1 for i in results if (int(picks[i]), *wl["eps"][eps_i[i]]) in plain_ref),
+            "plain_graphs_per_s": plain_gps, "all_ok": check["mismatch"] == 0 and check["bad_status"] == 0,
+            "checked_vs_oracle": check["checked"], "mismatch_vs_oracle": check["mismatch"],
+            "sets_checked": check["sets"], "cores_checked": check["cores"], "oracle_cache_s": round(t_oracle, 1),
             "pool": len(pool), "saturated": completed / wall < 0.95 * args.rate}
 
 
@@ -845,8 +905,9 @@ def main():
                 "config": {"workload": "serve", "desc": wl["desc"], "rate": args.rate, "duration_s": args.duration,
                            "pool": res["pool"]},
                 "serve": {k: res[k] for k in ("completed", "rejected", "offered", "offered_rate", "p50_us", "p99_us",
-                                              "batches", "saturated", "all_ok", "mismatch_vs_plain",
-                                              "checked_vs_plain")},
+                                              "batches", "saturated", "all_ok", "checked_vs_oracle",
+                                              "mismatch_vs_oracle", "sets_checked", "cores_checked",
+                                              "oracle_cache_s")},
                 "plain": {"graphs_per_s": res["plain_graphs_per_s"],
                           "form": "one request at a time: ingest + dsg_bahmani (+ dsg_kcore) per request"},
                 "served_over_plain": res["graphs_per_s"] / res["plain_graphs_per_s"]}), flush=True)
@@ -871,6 +932,8 @@ def main():
                 "batched_over_plain": res["value"] / world / res["plain_graphs_per_s"],
                 "batched_equals_plain": res["batched_equals_plain"],
                 "cpu_baseline": cpu, "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
+                "roofline": res["roofline"], "kernel_ms_per_step": res["kernel_ms"],
+                "run": {"tuning": res["tuning"], "grid_path_graphs": res["grid_path_graphs"]},
                 "host_generation_s": res["t_gen_s"], "ingest_s": res["t_ingest_s"],
                 "rounds_max": res["rounds_max"]}), flush=True)
         if world > 1:

@@ -271,6 +271,9 @@ typedef struct {
     uint8_t* out_set;       /* vtx_base[G], nullable: densest-set membership (host or device) */
     uint32_t* core;         /* vtx_base[G], nullable: core numbers (host or device; untouched
                                for graphs with want_core[g] == 0) */
+    uint64_t* stats;        /* 4, nullable (host): over the batch, the sum over graphs and rounds of
+                               |S_r|, the peels' alive-neighbour decrements, the adjacency entries
+                               (2m summed), and how many graphs the grid-wide kernels solved */
 } dsg_batch_result;
 
 /*
@@ -286,6 +289,13 @@ dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, void* stream
  * above 2^20; 0xffffffff keeps every graph in the block-per-graph launch.
  * DSG_BATCH_SPLIT.  Results never depend on it. */
 dsg_status dsg_set_batch_split(uint32_t min_work);
+/* Autotune dsg_batch_solve for this batch's class (device, floor(log2 G),
+ * floor(log2 of the summed 2m + n)): coordinate descent over the
+ * block-per-graph kernel's block size (256 / 512 / 1024), the hub threshold
+ * and the grid-wide split, timing whole solves of b (their results are
+ * discarded); later batches of the class use the winner.  Results never
+ * depend on it.  *trials (nullable) = solves timed. */
+dsg_status dsg_batch_autotune(const dsg_batch* b, uint32_t* trials);
 
 /* ------------------------------------------------------------- serving */
 
@@ -305,6 +315,12 @@ typedef struct {
     uint32_t max_pending;  /* queued, not yet admitted requests before DSG_EBUSY (0: 65536) */
     uint64_t hbm_budget;   /* device bytes admitted requests may hold (0: half the free memory) */
     uint32_t max_inflight; /* batches on the device at once, each on its own stream (0: 4) */
+    uint32_t ingest_threads; /* host threads ingesting admitted requests, each on its own stream (0: 4) */
+    uint64_t big_work;     /* a request whose 2 m_raw + n exceeds this is solved on its own by the
+                              grid-wide kernels on big_sms SMs, not in a block-per-graph batch
+                              (0: 2^23; UINT64_MAX: never) */
+    uint32_t big_sms;      /* SMs the grid-wide solves of big requests use (0: a quarter of them);
+                              the block-per-graph batches use the rest */
 } dsg_serve_config;
 
 #define DSG_REQ_BORROW 0x1u   /* src/dst stay valid and unchanged until the request completes: no copy */

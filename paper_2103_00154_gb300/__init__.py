@@ -439,17 +439,29 @@ class BatchSolver:
         self.q = np.ascontiguousarray(e[:, 1])
         self.want_core = None if want_core is None else np.ascontiguousarray(want_core, np.uint8)
 
-    def solve(self, out_set=None, core=None, stream=None):
+    def _batch(self):
+        return N.Batch(self.G, N.ptr(self.vtx_base), N.ptr(self.off), N.ptr(self.adj), N.ptr(self.p), N.ptr(self.q),
+                       N.ptr(self.want_core))
+
+    def solve(self, out_set=None, core=None, stream=None, stats=None):
+        """(E, V, R, best_round) per graph; stats (numpy uint64[4], optional)
+        receives the batch's byte-model counters (see dsg_batch_result)."""
         G = self.G
         E = np.zeros(max(G, 1), np.uint64)
         V = np.zeros(max(G, 1), np.uint64)
         R = np.zeros(max(G, 1), np.uint64)
         BR = np.zeros(max(G, 1), np.uint64)
-        b = N.Batch(G, N.ptr(self.vtx_base), N.ptr(self.off), N.ptr(self.adj), N.ptr(self.p), N.ptr(self.q),
-                    N.ptr(self.want_core))
-        r = N.BatchResult(N.ptr(E), N.ptr(V), N.ptr(R), N.ptr(BR), N.ptr(out_set), N.ptr(core))
+        b = self._batch()
+        r = N.BatchResult(N.ptr(E), N.ptr(V), N.ptr(R), N.ptr(BR), N.ptr(out_set), N.ptr(core), N.ptr(stats))
         N.check(lib().dsg_batch_solve(ctypes.byref(b), ctypes.byref(r), N.stream_handle(stream)), "batch_solve")
         return E[:G], V[:G], R[:G], BR[:G]
+
+    def autotune(self) -> int:
+        """dsg_batch_autotune on this batch; returns the number of timed solves."""
+        t = ctypes.c_uint32()
+        b = self._batch()
+        N.check(lib().dsg_batch_autotune(ctypes.byref(b), ctypes.byref(t)), "batch_autotune")
+        return int(t.value)
 
 
 # ------------------------------------------------------------------ serving
@@ -457,8 +469,9 @@ class Server:
     """Continuous-batching server (dsg_serve_*).  submit() returns a ticket;
     poll() returns a dict of the request's results or None while pending."""
 
-    def __init__(self, max_batch: int = 0, max_pending: int = 0, hbm_budget: int = 0, max_inflight: int = 0):
-        cfg = N.ServeConfig(max_batch, max_pending, hbm_budget, max_inflight)
+    def __init__(self, max_batch: int = 0, max_pending: int = 0, hbm_budget: int = 0, max_inflight: int = 0,
+                 ingest_threads: int = 0, big_work: int = 0, big_sms: int = 0):
+        cfg = N.ServeConfig(max_batch, max_pending, hbm_budget, max_inflight, ingest_threads, big_work, big_sms)
         h = ctypes.c_void_p()
         N.check(lib().dsg_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "serve_create")
         self._h = h

@@ -45,12 +45,14 @@ class Batch(c.Structure):
 
 
 class BatchResult(c.Structure):
-    _fields_ = [("E", _VP), ("V", _VP), ("rounds", _VP), ("best_round", _VP), ("out_set", _VP), ("core", _VP)]
+    _fields_ = [("E", _VP), ("V", _VP), ("rounds", _VP), ("best_round", _VP), ("out_set", _VP), ("core", _VP),
+                ("stats", _VP)]
 
 
 class ServeConfig(c.Structure):
     _fields_ = [("max_batch", c.c_uint32), ("max_pending", c.c_uint32), ("hbm_budget", c.c_uint64),
-                ("max_inflight", c.c_uint32)]
+                ("max_inflight", c.c_uint32), ("ingest_threads", c.c_uint32), ("big_work", c.c_uint64),
+                ("big_sms", c.c_uint32)]
 
 
 class Request(c.Structure):
@@ -105,6 +107,7 @@ _SIGS = [
     ("dsg_densest_core", c.c_int, [_VP, _VP, _VP, _VP, c.POINTER(CbdsResult)]),
     ("dsg_cbds", c.c_int, [_VP, _VP, _VP, _VP, c.POINTER(CbdsResult)]),
     ("dsg_batch_solve", c.c_int, [c.POINTER(Batch), c.POINTER(BatchResult), _VP]),
+    ("dsg_batch_autotune", c.c_int, [c.POINTER(Batch), _U32P]),
     ("dsg_serve_create", c.c_int, [c.POINTER(ServeConfig), c.POINTER(_VP)]),
     ("dsg_serve_submit", c.c_int, [_VP, c.POINTER(Request), _U64P]),
     ("dsg_serve_poll", c.c_int, [_VP, c.c_uint64, c.POINTER(Response), c.c_uint32]),

@@ -51,12 +51,14 @@ __device__ void peel_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
     const uint64_t p = a.p[g], q = a.q[g];
     uint64_t S = n, E = n ? (off[n] - off[0]) / 2 : 0;
     uint64_t best_E = E, best_V = S, best_round = 0, r = 0;
+    uint64_t sum_S = 0, ndec = 0;  // byte-model counters (thread-local; summed at the end)
     const uint32_t* alive = nullptr;
     uint32_t* next = alive_a;
     while (S > 0) {
         const uint32_t T = b_threshold(p, q, E, S);
         const uint32_t mark = kDeadB | (uint32_t)(r + 1);
         uint32_t nf = 0, ns = 0;
+        if (tid == 0) sum_S += S;
         // part 1: test every alive vertex against the round-start degrees
         for (uint64_t t = 0; t < S; t += TB) {
             uint64_t i = t + tid;
@@ -96,6 +98,7 @@ __device__ void peel_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
                 if (!(w[j] & kDeadB)) {
                     atomicSub(&st[u[j]], 1u);
                     ++dE;
+                    ++ndec;
                 } else if (w[j] == mark && u[j] > v[j]) {
                     ++dE;
                 }
@@ -113,6 +116,14 @@ __device__ void peel_block(const BatchArgs& a, uint32_t g, BatchSmem<TB>& sm) {
         }
         alive = next;
         next = (next == alive_a) ? alive_b : alive_a;
+    }
+    if (a.stats) {
+        ndec = warp_sum(ndec);
+        if ((tid & 31u) == 0 && ndec) atomicAdd(&a.stats[1], (unsigned long long)ndec);
+        if (tid == 0) {
+            atomicAdd(&a.stats[0], (unsigned long long)sum_S);
+            atomicAdd(&a.stats[2], (unsigned long long)(n ? off[n] - off[0] : 0));
+        }
     }
     if (tid == 0) {
         a.res[4 * (uint64_t)g + 0] = n ? best_E : 0;
@@ -227,18 +238,42 @@ __global__ void __launch_bounds__(TB) batch_kernel(BatchArgs a) {
     }
 }
 
-cudaError_t batch_launch(const BatchArgs& a, cudaStream_t s) {
-    constexpr int TB = 512;
-    if (a.G == 0) return cudaSuccess;
+template <int TB>
+static cudaError_t batch_launch_tb(const BatchArgs& a, cudaStream_t s, uint32_t max_grid) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TB>, TB, 0);
     if (e != cudaSuccess) return e;
     uint32_t slots = (uint32_t)(per_sm > 0 ? per_sm : 1) * (uint32_t)dev_info().sms;
+    if (max_grid && slots > max_grid) slots = max_grid;
     uint32_t grid = slots < a.G ? slots : a.G;
     LaunchScope ls("batch_solve", s);
     batch_kernel<TB><<<grid, TB, 0, s>>>(a);
     return cudaGetLastError();
 }
+
+cudaError_t batch_launch(const BatchArgs& a, cudaStream_t s, uint32_t block, uint32_t max_grid) {
+    if (a.G == 0) return cudaSuccess;
+    switch (block) {
+        case 256: return batch_launch_tb<256>(a, s, max_grid);
+        case 1024: return batch_launch_tb<1024>(a, s, max_grid);
+        default: return batch_launch_tb<512>(a, s, max_grid);
+    }
+}
+
+// Block slots of the block-per-graph kernel at `block` threads.
+static uint32_t batch_slots(uint32_t block) {
+    int per_sm = 0;
+    cudaError_t e;
+    switch (block) {
+        case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<256>, 256, 0); break;
+        case 1024: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<1024>, 1024, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<512>, 512, 0); break;
+    }
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    return (uint32_t)per_sm * (uint32_t)dev_info().sms;
+}
+
+uint32_t batch_slots_for(uint32_t block) { return batch_slots(block); }
 
 // want_core[g] read from host or device memory.
 static bool host_want_core(const uint8_t* want_core, uint32_t g, cudaStream_t s) {
@@ -371,17 +406,22 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
     DSG_TRY_CUDA(sc.get(&a.res, 4 * (size_t)G));
     DSG_TRY_CUDA(sc.get(&a.next, 1));
     DSG_TRY_CUDA(cudaMemsetAsync(a.next, 0, sizeof(unsigned long long), s));
-    const Tuning tu = current_tuning();
-    a.hot_deg = tu.hot_deg;
-    constexpr int TB = 512;
-    int per_sm = 0;
-    DSG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TB>, TB, 0));
-    const uint32_t slots = (uint32_t)std::max(1, per_sm) * (uint32_t)dev_info().sms;
     // Scheduling: a graph whose work is well above one block's share of the
     // batch would alone set the batch's makespan, so it is solved first by
     // the grid-wide kernels; the rest share one block-per-graph launch.
     uint64_t total_work = 0;
     for (uint32_t g = 0; g < G; ++g) total_work += work(g);
+    const Tuning tu = tuning_for_batch(G, total_work);
+    a.hot_deg = tu.hot_deg;
+    const uint32_t block = tu.batch_block ? tu.batch_block : 512;
+    const uint32_t slots = batch_slots(block);
+    unsigned long long* d_stats = nullptr;
+    if (r->stats) {
+        DSG_TRY_CUDA(sc.get(&d_stats, 3));
+        DSG_TRY_CUDA(cudaMemsetAsync(d_stats, 0, 3 * sizeof(unsigned long long), s));
+    }
+    a.stats = d_stats;
+    uint64_t big_sum_S = 0, big_dec = 0, big_entries = 0;
     const uint64_t share = total_work / slots;
     uint32_t nbig = 0;
     if (tu.batch_split)
@@ -399,8 +439,13 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
         view.owns = false;
         DSG_TRY_CUDA(cudaGetDevice(&view.device));
         view.stream = s;
-        dsg_status st = peel_into(&view, hp[g], hq[g], a.out_set ? a.out_set + vb[g] : nullptr, &res[4 * (size_t)g]);
+        uint64_t extra[2] = {0, 0};
+        dsg_status st = peel_into(&view, hp[g], hq[g], a.out_set ? a.out_set + vb[g] : nullptr, &res[4 * (size_t)g],
+                                  r->stats ? extra : nullptr);
         if (st != DSG_OK) return st;
+        big_sum_S += extra[0];
+        big_dec += extra[1];
+        big_entries += 2 * view.m;
         bool want = a.core && (!b->want_core || host_want_core(b->want_core, g, s));
         if (want) {
             st = run_kcore(&view, a.core + vb[g], nullptr, 0);
@@ -410,11 +455,7 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
     const uint32_t nsmall = G - nbig;
     a.order = d_order + nbig;
     a.G = nsmall;
-    if (nsmall) {
-        uint32_t grid = slots < nsmall ? slots : nsmall;
-        LaunchScope ls("batch_solve", s);
-        batch_kernel<TB><<<grid, TB, 0, s>>>(a);
-    }
+    if (nsmall) DSG_TRY_CUDA(batch_launch(a, s, block));
     DSG_TRY_CUDA(cudaGetLastError());
     std::vector<uint64_t> res_dev(4 * (size_t)G);
     DSG_TRY_CUDA(cudaMemcpyAsync(res_dev.data(), a.res, res_dev.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -430,6 +471,14 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
         if (r->V) r->V[g] = res[4 * (size_t)g + 1];
         if (r->rounds) r->rounds[g] = res[4 * (size_t)g + 2];
         if (r->best_round) r->best_round[g] = res[4 * (size_t)g + 3];
+    }
+    if (r->stats) {
+        unsigned long long h[3] = {0, 0, 0};
+        DSG_TRY_CUDA(cudaMemcpy(h, d_stats, sizeof(h), cudaMemcpyDeviceToHost));
+        r->stats[0] = h[0] + big_sum_S;
+        r->stats[1] = h[1] + big_dec;
+        r->stats[2] = h[2] + big_entries;
+        r->stats[3] = nbig;
     }
     return DSG_OK;
 }

@@ -26,11 +26,18 @@ struct BatchArgs {
     uint64_t* res;          // 4 per graph: E, V, rounds, best_round
     unsigned long long* next;
     uint32_t hot_deg;
+    unsigned long long* stats;  // nullable, 3 counters summed over the batch: sum over graphs and rounds of
+                                // |S_r|, alive-neighbour decrements of the peels, adjacency entries scanned
 };
 
 
 // Launch the block-per-graph kernel over a.order[0, a.G) on stream s
-// (asynchronous).  a.next must be zeroed and every table filled.
-cudaError_t batch_launch(const BatchArgs& a, cudaStream_t s);
+// (asynchronous) with `block` threads per block (256, 512 or 1024; 0: 512),
+// at most max_grid blocks (0: as many as fit).  a.next must be zeroed and
+// every table filled.
+cudaError_t batch_launch(const BatchArgs& a, cudaStream_t s, uint32_t block = 0, uint32_t max_grid = 0);
+
+// Blocks of `block` threads the block-per-graph kernel can keep resident on the GPU.
+uint32_t batch_slots_for(uint32_t block);
 
 }  // namespace dsg

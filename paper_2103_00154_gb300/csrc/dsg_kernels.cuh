@@ -31,7 +31,12 @@ struct Tuning {
                                  // finishes the levels on the compacted remaining graph (0: never)
     uint32_t batch_split = 0;    // batches: a graph whose work (2m + n) exceeds this is solved by the
                                  // grid-wide kernels (0: above twice a block's share and 2^20)
+    uint32_t batch_block = 512;  // batches: threads per block of the block-per-graph kernel
 };
+
+// Tuning of a batch of G graphs with `work` = sum of (2m + n): the autotuned
+// entry of its class if there is one, else current_tuning().
+Tuning tuning_for_batch(uint32_t G, uint64_t work);
 
 Tuning current_tuning();
 
@@ -65,7 +70,9 @@ dsg_status ingest_from_csr_entries(uint32_t n, const uint64_t* off, const uint32
 // One peel on a graph (any dsg_graph, including a view into a packed batch):
 // set_dev (device, nullable) gets the densest-set mask; out4 = E, V, rounds,
 // best_round.
-dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4]);
+// extra2 (nullable): sum over the rounds of |S_r| and the alive-neighbour decrements.
+dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4],
+                     uint64_t* extra2 = nullptr);
 
 // Core numbers of a graph into core_out (host or device); stats nullable.
 dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,

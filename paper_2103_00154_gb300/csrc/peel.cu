@@ -24,6 +24,7 @@
 #include <cstdlib>
 #include <string>
 #include <thread>
+#include <vector>
 
 #include "dsg_common.cuh"
 #include "dsg_kernels.cuh"
@@ -296,9 +297,23 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
                            uint64_t hist_cap_out, uint32_t* peel_round_out, uint8_t* set_out, PeelCtl* ctl_host,
                            uint64_t* trace_dev = nullptr, uint64_t trace_cap = 0);
 
-dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4]) {
+dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4],
+                     uint64_t* extra2) {
     PeelCtl c;
-    dsg_status st = run_peel(g, p, q, nullptr, nullptr, 0, nullptr, set_dev, &c);
+    dsg_status st;
+    if (extra2 && g->n) {
+        // the byte model's counters too: sum of |S_r| over the rounds (from the history) and the decrements
+        const uint64_t cap = dsg_round_bound(g->n, p, q) + 1;
+        std::vector<uint64_t> hs(cap);
+        st = run_peel(g, p, q, hs.data(), nullptr, cap, nullptr, set_dev, &c);
+        if (st != DSG_OK) return st;
+        uint64_t sum = 0;
+        for (uint64_t r = 0; r < c.rounds && r < cap; ++r) sum += hs[r];
+        extra2[0] = sum;
+        extra2[1] = c.dec;
+    } else {
+        st = run_peel(g, p, q, nullptr, nullptr, 0, nullptr, set_dev, &c);
+    }
     if (st != DSG_OK) return st;
     out4[0] = g->n ? c.best_E : 0;
     out4[1] = g->n ? c.best_V : 0;

@@ -4,13 +4,19 @@
 //   submit  copies the request into host memory the server owns and queues
 //           it (DSG_EBUSY when the queue is full: back-pressure);
 //   worker  (one host thread per server) admits queued requests while their
-//           device-memory charge fits the budget, ingests each on the ingest
-//           stream into a resident graph, and whenever one of its
-//           max_inflight solve streams is free launches one block-per-graph
-//           launch over everything ingested so far on that stream; while
-//           batches run it keeps admitting and ingesting new arrivals, which
-//           form the next batch; a finished batch's results are copied out,
-//           its graphs freed and their charge returned to the budget;
+//           device-memory charge fits the budget and hands them to the
+//           ingest threads, and whenever one of its max_inflight solve
+//           streams is free launches one block-per-graph launch over
+//           everything ingested so far on that stream; while batches run,
+//           new arrivals keep being admitted and ingested, and form the next
+//           batch; a finished batch's results are copied out, its graphs
+//           freed and their charge returned to the budget;
+//   ingest  (ingest_threads host threads, each with its own stream) turn
+//           admitted requests into resident graphs; a request above
+//           big_work goes to the big-request thread, the rest to the batches;
+//   big     (one host thread) solves big requests one at a time with the
+//           grid-wide kernels on big_sms SMs (the batches get the others), so
+//           one large graph never holds a batch of small ones back;
 //   poll    waits (bounded) for one ticket's completion.
 // A request's results do not depend on what it is batched with: each graph is
 // solved by its own block with its own state.
@@ -70,8 +76,15 @@ struct dsg_server {
     size_t in_use = 0;
     bool stop = false;
     std::thread worker;
-    cudaStream_t s_ingest = nullptr;
     std::vector<cudaStream_t> s_solve;  // one per batch that may be in flight
+    // ingest threads and the big-request thread
+    std::condition_variable cv_ingest, cv_big;
+    std::deque<dsg::ServeReq*> to_ingest, big;
+    std::vector<std::thread> ingesters;
+    std::vector<cudaStream_t> s_ingest;
+    std::thread big_worker;
+    cudaStream_t s_big = nullptr;
+    bool stop_helpers = false;
     // statistics
     uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, batches = 0;
     std::vector<double> lat_us;
@@ -118,10 +131,15 @@ static void finish_request(dsg_server* s, ServeReq* r, dsg_status st) {
     s->cv_done.notify_all();
 }
 
-// Ingest one admitted request on the ingest stream (synchronous for that stream only).
-static void ingest_one(dsg_server* s, ServeReq* r) {
+static bool is_big(const dsg_server* s, const ServeReq* r) {
+    return s->cfg.big_work != UINT64_MAX && 2 * r->m_raw + r->n > s->cfg.big_work;
+}
+
+// Ingest one admitted request on stream st (synchronous for that stream only)
+// and hand it to the batches or to the big-request thread.
+static void ingest_one(dsg_server* s, ServeReq* r, cudaStream_t st_ing) {
     dsg_graph* g = nullptr;
-    dsg_status st = dsg_graph_from_edges(r->n, r->m_raw, r->src, r->dst, 0, s->s_ingest, &g);
+    dsg_status st = dsg_graph_from_edges(r->n, r->m_raw, r->src, r->dst, 0, st_ing, &g);
     if (r->owned) {
         free(r->src);
         free(r->dst);
@@ -133,8 +151,69 @@ static void ingest_one(dsg_server* s, ServeReq* r) {
     }
     r->g = g;
     r->m = g->m;
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->ready.push_back(r);
+    const bool big = is_big(s, r);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (big) s->big.push_back(r);
+        else s->ready.push_back(r);
+    }
+    if (big) s->cv_big.notify_one();
+    else s->cv_work.notify_one();
+}
+
+static void ingest_main(dsg_server* s, cudaStream_t st) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        ServeReq* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_ingest.wait(lk, [&] { return s->stop_helpers || !s->to_ingest.empty(); });
+            if (s->to_ingest.empty()) return;  // stopping, nothing left
+            r = s->to_ingest.front();
+            s->to_ingest.pop_front();
+        }
+        ingest_one(s, r, st);
+    }
+}
+
+// A big request alone: the peel (and core numbers) by the grid-wide kernels,
+// capped at big_sms blocks of one per SM, on the big stream.
+static void solve_big(dsg_server* s, ServeReq* r) {
+    dsg_graph view = *r->g;
+    view.owns = false;
+    view.stream = s->s_big;
+    view.max_blocks = s->cfg.big_sms;
+    view.force_block = 1024;
+    dsg_status st = DSG_OK;
+    uint8_t* set_dev = nullptr;
+    if (r->out_set && r->n) {
+        if (dev_alloc((void**)&set_dev, r->n, s->s_big) != cudaSuccess) st = DSG_ENOMEM;
+    }
+    if (st == DSG_OK) st = peel_into(&view, r->p, r->q, set_dev, r->res);
+    if (st == DSG_OK && r->out_set && r->n &&
+        (cudaMemcpyAsync(r->out_set, set_dev, r->n, cudaMemcpyDeviceToHost, s->s_big) != cudaSuccess ||
+         cudaStreamSynchronize(s->s_big) != cudaSuccess))
+        st = DSG_ECUDA;
+    if (set_dev) dev_free(set_dev, s->s_big);
+    if (st == DSG_OK && r->want_core && r->core && r->n) st = run_kcore(&view, r->core, nullptr, 0);
+    cudaStreamSynchronize(s->s_big);
+    finish_request(s, r, st);
+}
+
+static void big_main(dsg_server* s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        ServeReq* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_big.wait(lk, [&] { return s->stop_helpers || !s->big.empty(); });
+            if (s->big.empty()) return;
+            r = s->big.front();
+            s->big.pop_front();
+        }
+        solve_big(s, r);
+        s->cv_work.notify_one();
+    }
 }
 
 // Build the tables of one batch and launch it on the solve stream.
@@ -204,8 +283,13 @@ static dsg_status launch_batch(dsg_server* s, Inflight& f, cudaStream_t ss) {
     a.res = reinterpret_cast<uint64_t*>(base + o_res);
     a.next = reinterpret_cast<unsigned long long*>(base + o_next);
     a.hot_deg = 0;
+    a.stats = nullptr;
     f.d_res = a.res;
-    DSG_TRY_CUDA(batch_launch(a, ss));
+    // the batches leave the big-request thread's share of the SMs free
+    const uint32_t sms = (uint32_t)dev_info().sms;
+    const uint32_t big_sms = s->cfg.big_work == UINT64_MAX ? 0 : std::min(s->cfg.big_sms, sms - 1);
+    const uint32_t cap = (uint32_t)((uint64_t)batch_slots_for(512) * (sms - big_sms) / sms);
+    DSG_TRY_CUDA(batch_launch(a, ss, 512, cap ? cap : 1));
     DSG_TRY_CUDA(cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming));
     DSG_TRY_CUDA(cudaEventRecord(f.done_ev, ss));
     // (the pageable staging vector may go: a host-to-device copy from pageable
@@ -254,26 +338,27 @@ static void worker_main(dsg_server* s) {
         return false;
     };
     for (;;) {
-        std::vector<ServeReq*> admit;
+        size_t admitted_now = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (!any_running() && s->pending.empty() && s->ready.empty()) {
-                if (s->stop) break;
+                // stop once every admitted request has completed (ingest and big threads included)
+                if (s->stop && s->admitted == s->completed) break;
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
-            // admit in arrival order while the budget allows
+            // admit in arrival order while the budget allows; the ingest threads take them
             while (!s->pending.empty()) {
                 ServeReq* r = s->pending.front();
                 if (s->in_use + r->charge > s->cfg.hbm_budget && s->in_use > 0) break;
                 s->pending.pop_front();
                 s->in_use += r->charge;
                 s->admitted++;
-                admit.push_back(r);
-                if (admit.size() >= 16) break;  // keep batch launches and completions responsive
+                s->to_ingest.push_back(r);
+                ++admitted_now;
             }
         }
-        for (ServeReq* r : admit) ingest_one(s, r);
+        if (admitted_now) s->cv_ingest.notify_all();
         // finished batches: results out, memory back
         for (size_t k = 0; k < K; ++k) {
             if (running[k] && cudaEventQuery(fl[k].done_ev) != cudaErrorNotReady) {
@@ -302,10 +387,10 @@ static void worker_main(dsg_server* s) {
                 running[k] = true;
             }
         }
-        if (any_running() && admit.empty()) {
-            // nothing to ingest: wait a little for arrivals or completions rather than spin
+        {
+            // wait a little for arrivals, ingests or completions rather than spin
             std::unique_lock<std::mutex> lk(s->mu);
-            if (s->pending.empty()) s->cv_work.wait_for(lk, std::chrono::microseconds(100));
+            if (s->pending.empty() && s->ready.empty()) s->cv_work.wait_for(lk, std::chrono::microseconds(100));
         }
     }
     for (size_t k = 0; k < K; ++k)
@@ -327,13 +412,19 @@ dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out) {
     if (!s->cfg.max_batch) s->cfg.max_batch = 1024;
     if (!s->cfg.max_pending) s->cfg.max_pending = 1u << 16;
     if (!s->cfg.max_inflight) s->cfg.max_inflight = 4;
+    if (!s->cfg.ingest_threads) s->cfg.ingest_threads = 4;
+    if (!s->cfg.big_work) s->cfg.big_work = 1ull << 23;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess && !s->cfg.hbm_budget) {
         size_t fr = 0, tot = 0;
         e = cudaMemGetInfo(&fr, &tot);
         s->cfg.hbm_budget = fr / 2;
     }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_ingest, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !s->cfg.big_sms) s->cfg.big_sms = std::max(1, dev_info().sms / 4);
+    s->s_ingest.assign(s->cfg.ingest_threads, nullptr);
+    for (uint32_t k = 0; k < s->cfg.ingest_threads && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&s->s_ingest[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_big, cudaStreamNonBlocking);
     s->s_solve.assign(s->cfg.max_inflight, nullptr);
     for (uint32_t k = 0; k < s->cfg.max_inflight && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&s->s_solve[k], cudaStreamNonBlocking);
@@ -343,6 +434,8 @@ dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out) {
         return DSG_ECUDA;
     }
     s->t0 = now_us();
+    for (uint32_t k = 0; k < s->cfg.ingest_threads; ++k) s->ingesters.emplace_back(ingest_main, s, s->s_ingest[k]);
+    s->big_worker = std::thread(big_main, s);
     s->worker = std::thread(worker_main, s);
     *out = s;
     return DSG_OK;
@@ -468,7 +561,16 @@ void dsg_serve_destroy(dsg_server* s) {
         s->stop = true;
     }
     s->cv_work.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    if (s->worker.joinable()) s->worker.join();  // every admitted request completed
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop_helpers = true;
+    }
+    s->cv_ingest.notify_all();
+    s->cv_big.notify_all();
+    for (auto& t : s->ingesters)
+        if (t.joinable()) t.join();
+    if (s->big_worker.joinable()) s->big_worker.join();
     for (auto& kv : s->by_ticket) {
         if (kv.second->owned) {
             free(kv.second->src);
@@ -477,7 +579,9 @@ void dsg_serve_destroy(dsg_server* s) {
         if (kv.second->g) dsg_graph_free(kv.second->g);
         delete kv.second;
     }
-    cudaStreamDestroy(s->s_ingest);
+    for (cudaStream_t st : s->s_ingest)
+        if (st) cudaStreamDestroy(st);
+    if (s->s_big) cudaStreamDestroy(s->s_big);
     for (cudaStream_t st : s->s_solve)
         if (st) cudaStreamDestroy(st);
     delete s;

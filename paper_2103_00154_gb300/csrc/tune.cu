@@ -129,6 +129,7 @@ extern "C" dsg_status dsg_get_tuning(uint32_t* block, uint32_t* blocks_per_sm, u
 
 #include <map>
 #include <string>
+#include <vector>
 
 namespace dsg {
 
@@ -195,6 +196,9 @@ static int load_table_locked(const char* path) {
         parse_u32(obj.c_str(), "local_work", &t.local_work);
         parse_u32(obj.c_str(), "inline_max", &t.inline_max);
         parse_u32(obj.c_str(), "kcore_tail", &t.tail_max);
+        parse_u32(obj.c_str(), "batch_split", &t.batch_split);
+        parse_u32(obj.c_str(), "batch_block", &t.batch_block);
+        if (t.batch_block != 256 && t.batch_block != 512 && t.batch_block != 1024) t.batch_block = 512;
         if (t.tail_max > kTailMaxVertices) t.tail_max = kTailMaxVertices;
         if ((t.block == 256 || t.block == 512 || t.block == 1024) && t.chunk_len >= 32 && t.short_max >= 1) {
             g_table[key] = t;
@@ -233,9 +237,21 @@ bool tuned_times(const dsg_graph* g, double* peel_ms, double* core_ms) {
     return true;
 }
 
-dsg_status run_kcore(const dsg_graph* g, uint32_t* core_out, uint64_t* stats, uint32_t nstats,
-                     uint64_t* trace_dev, uint64_t trace_cap, uint64_t* stamps);
-dsg_status peel_into(const dsg_graph* g, uint32_t p, uint32_t q, uint8_t* set_dev, uint64_t out4[4]);
+
+static std::string batch_key(uint32_t G, uint64_t work) {
+    char buf[400];
+    snprintf(buf, sizeof(buf), "%s|batch|%d:%d", device_key().c_str(), ilog2(G), ilog2(work));
+    return buf;
+}
+
+Tuning tuning_for_batch(uint32_t G, uint64_t work) {
+    if (g_forced) return *g_forced;
+    Tuning base = current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    ensure_table_loaded_locked();
+    auto it = g_table.find(batch_key(G, work));
+    return it == g_table.end() ? base : it->second;
+}
 
 // Device time of one solve with tuning t forced (best of `reps`), or a negative
 // value if the solve failed.
@@ -301,14 +317,13 @@ extern "C" dsg_status dsg_autotune(const dsg_graph* g, uint32_t eps_num, uint32_
                                    {&Tuning::chunk_len, {128, 256, 1024}, 3},
                                    {&Tuning::short_max, {16, 32, 64}, 3}};
         const Knob core_knobs[] = {{&Tuning::block, {256, 512, 1024}, 3},
-                                   {&Tuning::blocks_per_sm, {0, 1}, 2},
                                    {&Tuning::local_max, {256, 1024, 4096}, 3},
                                    {&Tuning::local_work, {4096, 16384, 65536}, 3},
                                    {&Tuning::inline_max, {256, 1024, 4096, 16384}, 4},
                                    {&Tuning::chunk_len, {256, 1024, 2048}, 3},
                                    {&Tuning::tail_max, {0, 16384, 32768, 131072}, 4}};
         const Knob* knobs = kernel == 0 ? peel_knobs : core_knobs;
-        const int nknobs = kernel == 0 ? 4 : 7;
+        const int nknobs = kernel == 0 ? 4 : 6;
         for (int kk = 0; kk < nknobs; ++kk) {
             for (int vi = 0; vi < knobs[kk].count; ++vi) {
                 Tuning cand = best;
@@ -355,9 +370,10 @@ extern "C" dsg_status dsg_tune_save(const char* path) {
         fprintf(f,
                 "  {\"key\": \"%s\", \"block\": %u, \"blocks_per_sm\": %u, \"short_max\": %u, \"chunk_len\": %u, "
                 "\"hot_deg\": %u, \"local_max\": %u, \"local_work\": %u, \"inline_max\": %u, \"kcore_tail\": %u, "
-                "\"ms\": %.4f}%s\n",
+                "\"batch_split\": %u, \"batch_block\": %u, \"ms\": %.4f}%s\n",
                 kv.first.c_str(), t.block, t.blocks_per_sm, t.short_max, t.chunk_len, t.hot_deg, t.local_max,
-                t.local_work, t.inline_max, t.tail_max, ms == g_table_ms.end() ? -1.0 : ms->second,
+                t.local_work, t.inline_max, t.tail_max, t.batch_split, t.batch_block,
+                ms == g_table_ms.end() ? -1.0 : ms->second,
                 ++i < g_table.size() ? "," : "");
     }
     fprintf(f, "]}\n");
@@ -403,5 +419,88 @@ extern "C" dsg_status dsg_tune_lookup(const dsg_graph* g, uint32_t kernel, uint3
     const uint32_t v[9] = {t.block,   t.blocks_per_sm, t.short_max,  t.chunk_len, t.hot_deg,
                            t.local_max, t.local_work,  t.inline_max, t.tail_max};
     memcpy(out, v, sizeof(v));
+    return DSG_OK;
+}
+
+// Batches: coordinate descent over the block-per-graph kernel's block size,
+// the hub threshold and the split between the grid-wide kernels and the
+// block-per-graph launch, timing whole dsg_batch_solve calls on the caller's
+// batch (results discarded); the winner is kept for the batch's class
+// (device, floor(log2 G), floor(log2 sum of 2m + n)).
+extern "C" dsg_status dsg_batch_autotune(const dsg_batch* b, uint32_t* trials_out) {
+    clear_error();
+    DSG_CHECK_ARG(b && b->vtx_base && b->off, "batch is NULL");
+    const uint32_t G = b->num_graphs;
+    if (G == 0) return DSG_OK;
+    std::vector<uint64_t> vb(G + 1);
+    DSG_TRY_CUDA(copy_any(vb.data(), b->vtx_base, (G + 1) * sizeof(uint64_t), nullptr));
+    uint64_t total = 0;
+    DSG_TRY_CUDA(copy_any(&total, b->off + vb[G], sizeof(uint64_t), nullptr));
+    DSG_TRY_CUDA(cudaDeviceSynchronize());
+    const uint64_t work = total + vb[G];
+    std::vector<uint64_t> E(G), V(G);
+    dsg_batch_result r;
+    memset(&r, 0, sizeof(r));
+    r.E = E.data();
+    r.V = V.data();
+    uint32_t trials = 0;
+    auto time_one = [&](const Tuning& t) -> double {
+        g_forced = &t;
+        double best = -1;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, nullptr);
+            dsg_status st = dsg_batch_solve(b, &r, nullptr);
+            cudaEventRecord(e1, nullptr);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st != DSG_OK) {
+                best = -1;
+                break;
+            }
+            if (best < 0 || ms < best) best = ms;
+        }
+        g_forced = nullptr;
+        ++trials;
+        return best;
+    };
+    Tuning best = tuning_for_batch(G, work);
+    double t_best = time_one(best);
+    if (t_best < 0) return DSG_ECUDA;
+    struct Knob {
+        uint32_t Tuning::*field;
+        uint32_t values[4];
+        int count;
+    };
+    const Knob knobs[] = {{&Tuning::batch_block, {256, 512, 1024}, 3},
+                          {&Tuning::hot_deg, {0, 1024, 16384}, 3},
+                          {&Tuning::batch_split, {0, 1u << 22, 0xffffffffu}, 3}};
+    for (const Knob& k : knobs) {
+        for (int vi = 0; vi < k.count; ++vi) {
+            Tuning cand = best;
+            cand.*(k.field) = k.values[vi];
+            if (cand.*(k.field) == best.*(k.field)) continue;
+            const double t = time_one(cand);
+            if (t >= 0 && t < 0.98 * t_best) {
+                best = cand;
+                t_best = t;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        ensure_table_loaded_locked();
+        const std::string key = batch_key(G, work);
+        g_table[key] = best;
+        g_table_ms[key] = t_best;
+    }
+    if (trials_out) *trials_out = trials;
+    const char* e = getenv("DSG_TUNE_FILE");
+    if (e && *e) dsg_tune_save(e);
     return DSG_OK;
 }
