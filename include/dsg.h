@@ -163,18 +163,19 @@ uint64_t dsg_round_bound(uint32_t n, uint32_t eps_num, uint32_t eps_den);
  *   stream       cudaStream_t to run on (NULL: default stream).  Every call
  *                waits for this stream twice: it reads off[n] back before
  *                the launch and the results after it.
- * Limits: the scratch is eight arrays, each rounded up to a multiple of 256
+ * Limits: the scratch is nine arrays, each rounded up to a multiple of 256
  * bytes: four of 4n bytes (vertex state, two alive lists, failed list), the
- * chunk items 8(n + 2m/chunk_len + 1) bytes, two round histories of
- * 8(dsg_round_bound(n, p, q) + 1) bytes, and a control block of about 1 KB;
- * chunk_len is the current tuning's (dsg_set_tuning; 256 by default).  A
- * graph whose scratch exceeds 64 MiB is rejected with DSG_EINVAL before any
- * GPU work (with eps > 0 and the default chunk_len that admits n up to about
- * 2.7 million at m = 8n).
+ * chunk items 8(n + 2m/chunk_len + 1) bytes, the status map 4 ceil(n/16)
+ * bytes, two round histories of 8(dsg_round_bound(n, p, q) + 1) bytes, and a
+ * control block of about 1 KB; chunk_len is the current tuning's
+ * (dsg_set_tuning; 256 by default).  A graph whose scratch exceeds 64 MiB is
+ * rejected with DSG_EINVAL before any GPU work (with eps > 0 and the default
+ * chunk_len that admits n up to about 2.7 million at m = 8n).
  * The first call in each CUDA context (the first on a device, and the first
  * after that device's context was destroyed and made again) looks the
- * buffer's device address up, with the device current; make that first call
- * before any CUDA stream capture.  All calls share the one buffer and it
+ * buffer's device address up, with the device current.  Because every call
+ * synchronises its stream (above), no call can be made on a stream that is
+ * being captured into a CUDA graph.  All calls share the one buffer and it
  * keeps the last call's contents: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  */

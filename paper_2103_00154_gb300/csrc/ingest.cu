@@ -825,10 +825,82 @@ __global__ void __launch_bounds__(256) sort_warp_rows(const uint32_t* __restrict
     }
 }
 
-// Rows of 1025..8192 entries: one block of 8 warps per row.  Each active warp
-// sorts 1024 values in registers; merges with block size 2048..p2 run their
-// cross-warp steps (distance >= 1024) through shared memory and the rest in
-// registers.
+// Sorting by one block of kBlockWarps warps (each warp sorts 1024 values in
+// registers; merges with block size 2048..p2 run their cross-warp steps,
+// distance >= 1024, through shared memory and the rest in registers), then
+// keeping the first of each run of equal values.
+template <uint32_t kBlockWarps>
+struct BlockSortSmem {
+    uint32_t s[kBlockWarps * 1024];
+    uint32_t wlast[kBlockWarps];
+    uint32_t wcount[kBlockWarps];
+};
+
+// in[0, len), 1 <= len <= kBlockWarps * 1024, sorted and de-duplicated into
+// out[0, kept) (out may be in: every value is in registers before any is
+// written); returns kept.  Every thread of the block calls it.
+template <uint32_t kBlockWarps>
+__device__ __forceinline__ uint32_t block_sort_unique(const uint32_t* in, uint32_t len, uint32_t* out,
+                                                      BlockSortSmem<kBlockWarps>& sm) {
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t base = w * 1024;
+    uint32_t p2 = 2048;
+    while (p2 < len) p2 <<= 1;
+    const bool active = base < p2;
+    uint32_t x[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        uint32_t i = base + (uint32_t)e * 32 + lane;
+        x[e] = (active && i < len) ? in[i] : kPad;
+    }
+    if (active) bitonic_sort<32, 1024>(x, base, lane);
+    for (uint32_t k = 2048; k <= p2; k <<= 1) {
+        for (uint32_t j = k >> 1; j >= 1024; j >>= 1) {
+            if (active) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) sm.s[base + (uint32_t)e * 32 + lane] = x[e];
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    uint32_t i = base + (uint32_t)e * 32 + lane;
+                    uint32_t y = sm.s[i ^ j];
+                    bool asc = (i & k) == 0;
+                    bool lower = (i & j) == 0;
+                    x[e] = (lower == asc) ? min(x[e], y) : max(x[e], y);
+                }
+            }
+            __syncthreads();
+        }
+        if (active) bitonic_merge<32, 512>(x, base, k, lane);
+    }
+    // de-duplicate across the block: each warp needs the previous warp's last value
+    if (lane == 31) sm.wlast[w] = x[31];
+    __syncthreads();
+    uint32_t prev_in = (w == 0 || !active) ? kPad : sm.wlast[w - 1];
+    // count first, then write at the prefix of the warps' counts
+    uint32_t mine = 0;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        uint32_t up = __shfl_up_sync(kFullMask, x[e], 1);
+        uint32_t last_prev = e == 0 ? prev_in : __shfl_sync(kFullMask, x[e > 0 ? e - 1 : 0], 31);
+        uint32_t prev = lane == 0 ? last_prev : up;
+        mine += __popc(__ballot_sync(kFullMask, x[e] != kPad && x[e] != prev));
+    }
+    if (lane == 0) sm.wcount[w] = active ? mine : 0;
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+    for (uint32_t q = 0; q < kBlockWarps; ++q) {
+        if (q < w) off += sm.wcount[q];
+        total += sm.wcount[q];
+    }
+    if (active) warp_unique_write<32>(x, prev_in, lane, out + off);
+    __syncthreads();
+    return total;
+}
+
+// Rows of 1025..8192 entries: one block of kBlockWarps warps per row.
 template <uint32_t kBlockWarps>
 __global__ void __launch_bounds__(kBlockWarps * 32) sort_block_rows(const uint32_t* __restrict__ list,
                                                                     uint32_t count,
@@ -836,75 +908,157 @@ __global__ void __launch_bounds__(kBlockWarps * 32) sort_block_rows(const uint32
                                                                     const uint32_t* __restrict__ cnt,
                                                                     uint32_t* __restrict__ tmp,
                                                                     uint32_t* __restrict__ newlen) {
-    __shared__ uint32_t s[kBlockWarps * 1024];
-    __shared__ uint32_t wlast[kBlockWarps];
-    __shared__ uint32_t wcount[kBlockWarps];
-    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    const uint32_t base = w * 1024;
+    __shared__ BlockSortSmem<kBlockWarps> sm;
     for (uint32_t r = blockIdx.x; r < count; r += gridDim.x) {
-        uint32_t v = list[r];
-        uint32_t len = cnt[v];
-        uint64_t b = start[v];
-        uint32_t p2 = 2048;
-        while (p2 < len) p2 <<= 1;
-        const bool active = base < p2;
-        uint32_t x[32];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            uint32_t i = base + (uint32_t)e * 32 + lane;
-            x[e] = (active && i < len) ? tmp[b + i] : kPad;
-        }
-        if (active) bitonic_sort<32, 1024>(x, base, lane);
-        for (uint32_t k = 2048; k <= p2; k <<= 1) {
-            for (uint32_t j = k >> 1; j >= 1024; j >>= 1) {
-                if (active) {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) s[base + (uint32_t)e * 32 + lane] = x[e];
-                }
-                __syncthreads();
-                if (active) {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        uint32_t i = base + (uint32_t)e * 32 + lane;
-                        uint32_t y = s[i ^ j];
-                        bool asc = (i & k) == 0;
-                        bool lower = (i & j) == 0;
-                        x[e] = (lower == asc) ? min(x[e], y) : max(x[e], y);
-                    }
-                }
-                __syncthreads();
-            }
-            if (active) bitonic_merge<32, 512>(x, base, k, lane);
-        }
-        // de-duplicate across the block: each warp needs the previous warp's last value
-        if (lane == 31) wlast[w] = x[31];
-        __syncthreads();
-        uint32_t prev_in = (w == 0 || !active) ? kPad : wlast[w - 1];
-        // count first, then write at the prefix of the warps' counts
-        uint32_t mine = 0;
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            uint32_t up = __shfl_up_sync(kFullMask, x[e], 1);
-            uint32_t last_prev = e == 0 ? prev_in : __shfl_sync(kFullMask, x[e > 0 ? e - 1 : 0], 31);
-            uint32_t prev = lane == 0 ? last_prev : up;
-            mine += __popc(__ballot_sync(kFullMask, x[e] != kPad && x[e] != prev));
-        }
-        if (lane == 0) wcount[w] = active ? mine : 0;
-        __syncthreads();
-        uint32_t off = 0, total = 0;
-        for (uint32_t q = 0; q < kBlockWarps; ++q) {
-            if (q < w) off += wcount[q];
-            total += wcount[q];
-        }
-        if (active) warp_unique_write<32>(x, prev_in, lane, tmp + b + off);
-        if (threadIdx.x == 0) newlen[v] = total;
-        __syncthreads();
+        const uint32_t v = list[r];
+        uint32_t* row = tmp + start[v];
+        const uint32_t kept = block_sort_unique<kBlockWarps>(row, cnt[v], row, sm);
+        if (threadIdx.x == 0) newlen[v] = kept;
     }
 }
 
-// ---- giant rows (> kBlockRowMax entries): one block per row sorts it by an
-// LSD radix sort on 8-bit digits of the neighbour ids (as many passes as n's
-// ids need), ping-ponging between the row's place in tmp and in spare.  Each
+// ---- giant rows (> kBlockRowMax entries), one block of 8 warps per row:
+// splitters taken from a sorted sample of the row (1,024 values spread over
+// it) cut its values into ranges of about kSplitTarget entries; the row is
+// counted and scattered by range into the spare buffer (equal values share a
+// range, so no run of equal ids crosses two ranges), each range is sorted and
+// de-duplicated by the block like a block row, and the ranges' unique values
+// are copied back, in range order, to the row's place in tmp.  A row with a
+// range above kBlockRowMax entries (a very skewed row) goes to a list that
+// the radix kernel below sorts instead.
+constexpr uint32_t kSplitTarget = 5000;
+constexpr uint32_t kSplitMaxRanges = 64;
+
+struct SplitSmem {
+    BlockSortSmem<8> bs;
+    uint32_t spl[kSplitMaxRanges];         // splitters: range of x = number of splitters <= x
+    uint32_t rcnt[kSplitMaxRanges];        // entries per range ...
+    uint32_t rcur[kSplitMaxRanges];        // ... scatter cursors ...
+    uint32_t rstart[kSplitMaxRanges + 1];  // ... first slot of each range
+    uint32_t kept[kSplitMaxRanges + 1];    // unique values per range, then their exclusive prefix
+    uint32_t row, nsp, too_big;
+};
+
+__device__ __forceinline__ uint32_t split_range(const uint32_t* spl, uint32_t nsp, uint32_t x) {
+    uint32_t lo = 0, hi = nsp;  // first splitter > x
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (spl[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) giant_split_kernel(const uint32_t* __restrict__ list, uint32_t count,
+                                                          const uint64_t* __restrict__ start,
+                                                          const uint32_t* __restrict__ cnt, uint32_t* __restrict__ tmp,
+                                                          uint32_t* __restrict__ spare, uint32_t* __restrict__ newlen,
+                                                          uint32_t* __restrict__ ticket,
+                                                          uint32_t* __restrict__ skewed, uint32_t* __restrict__ nskewed) {
+    __shared__ SplitSmem sm;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sm.row = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const uint32_t r = sm.row;
+        if (r >= count) break;
+        const uint32_t v = list[r];
+        const uint32_t L = cnt[v];
+        uint32_t* A = tmp + start[v];
+        uint32_t* B = spare + start[v];
+        const uint32_t nr = min(kSplitMaxRanges, (L + kSplitTarget - 1) / kSplitTarget);
+        // ---- the sample, sorted by warp 0; splitters at its nr-quantiles
+        if (w == 0) {
+            uint32_t x[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) x[e] = A[((uint64_t)((uint32_t)e * 32 + lane) * L) >> 10];
+            bitonic_sort<32, 1024>(x, 0, lane);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) sm.bs.s[(uint32_t)e * 32 + lane] = x[e];
+        }
+        if (tid < kSplitMaxRanges) {
+            sm.rcnt[tid] = 0;
+            sm.rcur[tid] = 0;
+        }
+        __syncthreads();
+        if (tid + 1 < nr) sm.spl[tid] = sm.bs.s[((tid + 1) * 1024) / nr];
+        if (tid == 0) sm.nsp = nr - 1;
+        __syncthreads();
+        const uint32_t nsp = sm.nsp;
+        // ---- entries per range
+        for (uint32_t i0 = 0; i0 < L; i0 += 256) {
+            const uint32_t i = i0 + tid;
+            const uint32_t rg = i < L ? split_range(sm.spl, nsp, A[i]) : kSplitMaxRanges;
+            const uint32_t peers = __match_any_sync(kFullMask, rg);
+            if (rg < kSplitMaxRanges && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sm.rcnt[rg], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t c0 = lane < nr ? sm.rcnt[lane] : 0u, c1 = lane + 32 < nr ? sm.rcnt[lane + 32] : 0u;
+            const uint32_t i0 = warp_incl_scan(c0), i1 = warp_incl_scan(c1);
+            const uint32_t t0 = __shfl_sync(kFullMask, i0, 31);
+            const uint32_t tot = t0 + __shfl_sync(kFullMask, i1, 31);
+            sm.rstart[lane] = i0 - c0;
+            sm.rstart[lane + 32] = t0 + i1 - c1;
+            if (lane == 0) sm.rstart[kSplitMaxRanges] = tot;
+            const uint32_t big = __ballot_sync(kFullMask, c0 > kBlockRowMax || c1 > kBlockRowMax);
+            if (lane == 0) sm.too_big = big != 0;
+        }
+        __syncthreads();
+        if (sm.too_big) {
+            if (tid == 0) skewed[atomicAdd(nskewed, 1u)] = v;
+            continue;
+        }
+        // ---- scatter by range (order inside a range does not matter: it is sorted next)
+        for (uint32_t i0 = 0; i0 < L; i0 += 256) {
+            const uint32_t i = i0 + tid;
+            const uint32_t x = i < L ? A[i] : 0u;
+            const uint32_t rg = i < L ? split_range(sm.spl, nsp, x) : kSplitMaxRanges;
+            const uint32_t peers = __match_any_sync(kFullMask, rg);
+            const uint32_t leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (rg < kSplitMaxRanges && lane == leader) base = atomicAdd(&sm.rcur[rg], (uint32_t)__popc(peers));
+            base = __shfl_sync(kFullMask, base, leader);
+            if (rg < kSplitMaxRanges) B[sm.rstart[rg] + base + __popc(peers & lanemask_lt())] = x;
+        }
+        __syncthreads();
+        // ---- each range sorted and de-duplicated in place
+        for (uint32_t g = 0; g < nr; ++g) {
+            const uint32_t c = sm.rcnt[g];
+            uint32_t k = 0;
+            if (c) k = block_sort_unique<8>(B + sm.rstart[g], c, B + sm.rstart[g], sm.bs);
+            if (tid == 0) sm.kept[g] = k;
+        }
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t c0 = lane < nr ? sm.kept[lane] : 0u, c1 = lane + 32 < nr ? sm.kept[lane + 32] : 0u;
+            const uint32_t i0 = warp_incl_scan(c0), i1 = warp_incl_scan(c1);
+            const uint32_t t0 = __shfl_sync(kFullMask, i0, 31);
+            const uint32_t tot = t0 + __shfl_sync(kFullMask, i1, 31);
+            __syncwarp();
+            sm.kept[lane] = i0 - c0;
+            sm.kept[lane + 32] = t0 + i1 - c1;
+            if (lane == 0) {
+                sm.kept[kSplitMaxRanges] = tot;
+                newlen[v] = tot;
+            }
+        }
+        __syncthreads();
+        // ---- the ranges' unique values back to the row, in order
+        for (uint32_t g = 0; g < nr; ++g) {
+            const uint32_t k = (g + 1 < nr ? sm.kept[g + 1] : sm.kept[kSplitMaxRanges]) - sm.kept[g];
+            const uint32_t* src = B + sm.rstart[g];
+            uint32_t* dst = A + sm.kept[g];
+            for (uint32_t j = tid; j < k; j += 256) dst[j] = src[j];
+        }
+    }
+}
+
+// ---- skewed giant rows (a splitter range above kBlockRowMax entries): one
+// block per row sorts it by an LSD radix sort on 8-bit digits of the
+// neighbour ids (as many passes as n's ids need), ping-ponging between the
+// row's place in tmp and in spare; the rows come from a list whose length is
+// in device memory.  Each
 // pass is stable: a digit histogram of the row gives every digit's first
 // slot, then the row is walked in order one block-sized tile at a time, and
 // a key's slot is its digit's next free slot plus the number of earlier keys
@@ -920,7 +1074,8 @@ struct RadixSmem {
     uint32_t row, kept;
 };
 
-__global__ void __launch_bounds__(kRadixTB) giant_radix_kernel(const uint32_t* __restrict__ list, uint32_t count,
+__global__ void __launch_bounds__(kRadixTB) giant_radix_kernel(const uint32_t* __restrict__ list,
+                                                               const uint32_t* __restrict__ count_dev,
                                                                const uint64_t* __restrict__ start,
                                                                const uint32_t* __restrict__ cnt,
                                                                uint32_t* __restrict__ tmp,
@@ -935,7 +1090,7 @@ __global__ void __launch_bounds__(kRadixTB) giant_radix_kernel(const uint32_t* _
         if (tid == 0) sm.row = atomicAdd(ticket, 1u);
         __syncthreads();
         const uint32_t r = sm.row;
-        if (r >= count) break;
+        if (r >= *count_dev) break;
         const uint32_t v = list[r];
         const uint32_t len = cnt[v];
         uint32_t* A = tmp + start[v];
@@ -1227,14 +1382,23 @@ static dsg_status ingest_device(uint32_t n, uint64_t m_raw, const uint32_t* src,
         uint32_t nbits = 1;
         while (nbits < 32 && ((uint64_t)n - 1) >> nbits) ++nbits;
         const uint32_t passes = (nbits + 7) / 8;
-        // the bucket entries are no longer needed: their space is the radix sort's spare buffer
+        // the bucket entries are no longer needed: their space is the spare buffer of both sorts
         uint32_t* spare = reinterpret_cast<uint32_t*>(E1);
-        uint32_t* gticket;
-        DSG_TRY_CUDA(sc.get(&gticket, 1));
-        DSG_TRY_CUDA(cudaMemsetAsync(gticket, 0, sizeof(uint32_t), s));
-        const uint32_t g = std::min<uint32_t>(ng, sms);
-        LaunchScope ls_("ingest_giant_rows", s);
-        giant_radix_kernel<<<g, kRadixTB, 0, s>>>(glist, ng, start, cnt, tmp, spare, passes, newlen, gticket);
+        uint32_t *gticket, *skewed;  // gticket[0]: split rows taken, [1]: skewed rows listed, [2]: radix rows taken
+        DSG_TRY_CUDA(sc.get(&gticket, 3));
+        DSG_TRY_CUDA(sc.get(&skewed, ng));
+        DSG_TRY_CUDA(cudaMemsetAsync(gticket, 0, 3 * sizeof(uint32_t), s));
+        {
+            LaunchScope ls_("ingest_giant_rows", s);
+            giant_split_kernel<<<std::min<uint32_t>(ng, 2 * sms), 256, 0, s>>>(glist, ng, start, cnt, tmp, spare,
+                                                                             newlen, gticket, skewed, gticket + 1);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+        {
+            LaunchScope ls_("ingest_giant_skewed", s);
+            giant_radix_kernel<<<std::min<uint32_t>(ng, sms), kRadixTB, 0, s>>>(skewed, gticket + 1, start, cnt, tmp,
+                                                                              spare, passes, newlen, gticket + 2);
+        }
     }
     DSG_TRY_CUDA(cudaGetLastError());
     dsg_graph* g = new dsg_graph();

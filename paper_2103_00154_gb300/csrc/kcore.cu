@@ -314,14 +314,26 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
             if (nv == k) reach_k(u);
             else dmn = min(dmn, nv);
         };
-        // every neighbour of a drained vertex loses one degree at once (no
-        // read first: one memory round trip less per link of a cascade); a
-        // neighbour already at or below k gets it back in settle
+        // every neighbour of a drained vertex that is not taken yet (its claim
+        // bit, from a 1-bit-per-vertex map that stays in L2) loses one degree
+        // at once (no read of the degree first); a neighbour already at or
+        // below k, taken since its bit was read, gets it back in settle
         auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
-            uint32_t old[kBatch], need = 0;
+            uint32_t old[kBatch], cw[kBatch], need = 0;
+#ifdef DSG_DEBUG_BOUNDS
+            constexpr uint32_t kOutside = 0u;  // an id out of range reaches the bounds check below
+#else
+            constexpr uint32_t kOutside = 0xffffffffu;
+#endif
+#pragma unroll
+            for (uint32_t jj = 0; jj < kBatch; ++jj)
+                cw[jj] = !(valid >> jj & 1u) || u[jj] == v[jj] ? 0xffffffffu
+                         : u[jj] < n                         ? a.claim[u[jj] >> 5]
+                                                             : kOutside;
 #pragma unroll
             for (uint32_t jj = 0; jj < kBatch; ++jj) {
                 if (!(valid >> jj & 1u) || u[jj] == v[jj]) continue;
+                if (cw[jj] >> (u[jj] & 31u) & 1u) continue;  // taken: nothing to take from it
 #ifdef DSG_DEBUG_BOUNDS
                 if (u[jj] >= n) {
                     DSG_BOUND(ctl, 4, u[jj], n, level, (void)0);
@@ -396,11 +408,13 @@ __global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
                     in[u] = i < lim;
                     v[u] = in[u] ? (my_rem ? my_rem[i] : (uint32_t)i) : 0u;
                 }
+                // the degree first; the claim word only where the degree is at or
+                // below k (a vertex taken at an earlier level ended at its core
+                // number, below k, so one above k is never taken)
 #pragma unroll
-                for (uint32_t u = 0; u < kScanU; ++u) {
-                    dv[u] = in[u] ? deg[v[u]] : 0u;
-                    cw[u] = in[u] ? a.claim[v[u] >> 5] : 0u;
-                }
+                for (uint32_t u = 0; u < kScanU; ++u) dv[u] = in[u] ? deg[v[u]] : 0u;
+#pragma unroll
+                for (uint32_t u = 0; u < kScanU; ++u) cw[u] = (in[u] && dv[u] <= k) ? a.claim[v[u] >> 5] : 0u;
                 bool keep[kScanU], mine[kScanU];
 #pragma unroll
                 for (uint32_t u = 0; u < kScanU; ++u) {

@@ -9,18 +9,34 @@
 // the neighbours that remain, which changes no degree: a remaining vertex's
 // degree already counts exactly its remaining neighbours, and a drain never
 // lowers the degree of a vertex that is gone -- and then one cluster runs the
-// remaining levels with every vertex's degree, claim bit and queue slot in
+// remaining levels with every vertex's degree, row bounds and queue slot in
 // the distributed shared memory of the cluster: vertex i belongs to block
-// i % C.  Level k: each block scans its own vertices (a list of the ones not
-// yet taken, compacted every level) and claims those of degree <= k; a
-// drained vertex's neighbours above k lose one degree each (Algorithm 2's
-// drain, reading the degree first); a neighbour brought to k is claimed by
-// the decrementer and queued at its owner, so every block drains its own
-// vertices and a cascade spreads over the cluster.  A cluster-wide count of
-// claimed vertices not yet drained (plus one token per block until its scan
-// is done) reaching zero ends the level; the blocks then meet at a cluster
-// barrier and sum the level's claims and least degree above k, so every
-// block takes the same decisions.  Every wait is bounded (ERR_TIMEOUT).
+// i % C.
+//
+// Level k:
+//   scan: each block walks its own vertices not yet taken (a list compacted
+//     every level) and takes those of degree <= k into its queue; the scan
+//     takes are added to a cluster-wide pending count, and a cluster barrier
+//     separates the scan from the drain, so no degree changes while any
+//     block scans;
+//   every block copies the cluster's taken bits (the union of the blocks'
+//     own bitmaps) into its shared memory, so a drain skips a neighbour that
+//     is gone with a local look-up;
+//   drain: each block drains its queue in batches, all its threads spread
+//     over the batch's rows; a neighbour that is not gone loses one degree
+//     (a DSMEM atomic at its owner); if that brought it from k + 1 to k the
+//     decrementer is the one thread that does so: it reads the vertex's row
+//     bounds at the owner, asks L2 for the row, and queues the vertex at its
+//     owner (pending count up, a slot at the owner, one store of the owner's
+//     local index); if it was at or below k already (taken during this
+//     level) the decrement is undone, which leaves the degrees Algorithm 2's
+//     read-then-decrement drain leaves.  A block gives a batch's count back
+//     to the pending count once the batch and the takes it made are
+//     registered, so the count reaches zero only when the level's cascade is
+//     over; the owners drain, so a cascade spreads over the cluster;
+//   the blocks meet at a cluster barrier and sum the level's takes and least
+//   degree above k, so every block takes the same decisions.
+// Every wait is bounded (ERR_TIMEOUT).
 #include <cooperative_groups.h>
 
 #include "dsg_common.cuh"
@@ -31,8 +47,11 @@ namespace cg = cooperative_groups;
 namespace dsg {
 
 constexpr uint32_t kTailTB = 1024;
-constexpr uint32_t kTailVPC = 8192;   // vertices per block at most
-constexpr uint32_t kSlotEmpty = 0xffffffffu;
+constexpr uint32_t kTailC = 16;                       // blocks in the cluster
+constexpr uint32_t kTailVPC = kTailMaxVertices / kTailC;  // vertices per block at most
+constexpr uint32_t kTailWPB = kTailVPC / 32;          // bitmap words per block
+constexpr uint16_t kSlotEmpty = 0xffffu;
+constexpr uint32_t kOffMax = 0xffffffffu;             // compacted row offsets must stay below this
 
 struct TailStats {
     unsigned long long levels, rem_scanned, atomics, claims, stamps;
@@ -53,21 +72,34 @@ struct TailArgs {
 };
 
 struct TailSmem {
-    uint32_t deg[kTailVPC];
-    uint32_t claim[kTailVPC / 32];
-    uint16_t rem[2][kTailVPC];
-    uint2 q[kTailVPC];           // this block's vertices to drain at this level: (row start, length);
-                                 // x == kSlotEmpty until the claimer has written it
-    uint32_t start[kTailTB];     // a batch's rows: exclusive prefix of lengths ...
-    uint64_t beg[kTailTB];       // ... row starts
+    uint32_t deg[kTailVPC];            // this block's vertices' degrees (other blocks decrement them)
+    uint32_t rbeg[kTailVPC];           // ... their row starts and lengths in the compacted adjacency
+    uint32_t rlen[kTailVPC];
+    uint32_t taken[kTailWPB];          // this block's vertices taken into a level (written by this block)
+    uint32_t gone[kTailC * kTailWPB];  // copy of every block's taken bits, block b's at [b * kTailWPB]
+    uint16_t rem[2][kTailVPC];         // this block's vertices still to scan, by level parity
+    uint16_t q[kTailVPC];              // this level's queue of own vertices (local index); kSlotEmpty until
+                                       // the taker has written it
+    uint32_t start[kTailTB];           // a batch's rows: exclusive prefix of lengths ...
+    uint32_t beg[kTailTB];             // ... row starts
     uint32_t red[33];
     uint64_t red64[33];
     uint32_t qtail, nkeep, batch_n, batch_total, stop;
-    uint32_t pending[2];         // block 0 only, by level parity: claimed-not-drained vertices + block tokens
-    uint32_t pub_min[2], pub_claims[2], pub_err[2];  // a level's totals, by level parity
+    uint32_t pending;                  // block 0's copy: taken vertices of the level not yet drained
+    uint32_t pub_min[2], pub_claims[2], pub_err[2];  // a level's totals of this block, by level parity
     uint32_t tot_min, tot_err;
     unsigned long long tot_claims;
 };
+
+// Ask L2 to fetch adj[b, b + l) (rounded out to 16-byte boundaries; the
+// adjacency allocation is padded to 256 bytes, so the rounding stays inside it).
+__device__ __forceinline__ void prefetch_row(const uint32_t* adj, uint32_t b, uint32_t l) {
+    if (l == 0) return;
+    const uint64_t lo = (uint64_t)b & ~3ull, hi = ((uint64_t)b + l + 3) & ~3ull;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(adj + lo)),
+                 "r"((uint32_t)((hi - lo) * 4))
+                 : "memory");
+}
 
 __global__ void __launch_bounds__(kTailTB, 1) kcore_tail_kernel(TailArgs a) {
     extern __shared__ __align__(16) unsigned char tail_smem_raw[];
@@ -75,35 +107,39 @@ __global__ void __launch_bounds__(kTailTB, 1) kcore_tail_kernel(TailArgs a) {
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t C = cluster.num_blocks();
     const uint32_t rank = cluster.block_rank();
-    const uint32_t tid = threadIdx.x;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
     const uint32_t r = a.r;
     const uint32_t V = r > rank ? (r - rank + C - 1) / C : 0;  // this block's vertices: i = li * C + rank
-    // ---- degrees, claim bits, queue slots, the list of this block's vertices; least degree
+    const uint32_t wmax = ((r + C - 1) / C + 31) / 32;         // taken words in use per block
+    // ---- degrees, row bounds, the list of this block's vertices; least degree
     uint32_t mn = 0xffffffffu;
     for (uint32_t li = tid; li < V; li += kTailTB) {
-        const uint32_t d = a.cdeg[li * C + rank];
+        const uint32_t i = li * C + rank;
+        const uint32_t d = a.cdeg[i];
+        const uint64_t b0 = a.off[i], b1 = a.off[i + 1];
         sm.deg[li] = d;
+        sm.rbeg[li] = (uint32_t)b0;
+        sm.rlen[li] = (uint32_t)(b1 - b0);
         sm.rem[0][li] = (uint16_t)li;
         mn = min(mn, d);
     }
-    for (uint32_t w = tid; w < kTailVPC / 32; w += kTailTB) sm.claim[w] = 0;
-    for (uint32_t i = tid; i < kTailVPC; i += kTailTB) sm.q[i] = make_uint2(kSlotEmpty, 0u);
+    for (uint32_t w = tid; w < kTailWPB; w += kTailTB) sm.taken[w] = 0;
+    for (uint32_t i = tid; i < kTailVPC; i += kTailTB) sm.q[i] = kSlotEmpty;
     mn = block_min_u32(mn, sm.red);
     if (tid == 0) {
         sm.pub_min[1] = mn;
-        sm.pub_claims[1] = 0;
-        sm.pub_err[1] = 0;
         sm.qtail = 0;
-        sm.pending[0] = C;  // (block 0's copy is the one used) every block's token for level 0
-        sm.pending[1] = 0;
+        sm.pending = 0;
     }
     cluster.sync();
     uint32_t k = 0xffffffffu;
-    for (uint32_t q = 0; q < C; ++q) k = min(k, *cluster.map_shared_rank(&sm.pub_min[1], (int)q));
+    for (uint32_t b = 0; b < C; ++b) k = min(k, *cluster.map_shared_rank(&sm.pub_min[1], (int)b));
+    uint32_t* const pending0 = cluster.map_shared_rank(&sm.pending, 0);
     uint64_t visited = 0, level = 0, scanned = 0, natom = 0, nstamp = 0;
     uint32_t nrem = V;
     bool bad = false, timeout = false;
-    // trace pairs: kind 11 scan done, 12 drain done, 13 level over (block 0), 14 the level's claims
+    // trace pairs: kind 11 scan done, 12 drain done, 13 level over (block 0), 14 the level's claims;
+    // block 0's batches: 15 batch taken (time), 16 its vertices << 32 | its entries, 17 batch drained (time)
     auto stamp = [&](uint32_t kind, uint64_t val) {
         if (a.trace && rank == 0 && tid == 0 && 2 * nstamp + 1 < a.trace_cap) {
             a.trace[2 * nstamp] = val;
@@ -115,189 +151,229 @@ __global__ void __launch_bounds__(kTailTB, 1) kcore_tail_kernel(TailArgs a) {
         const uint32_t par = (uint32_t)(level & 1);
         const uint16_t* cur = sm.rem[par];
         uint16_t* nxt = sm.rem[par ^ 1u];
-        uint32_t lmin = 0xffffffffu, lclaims = 0;
-        uint32_t* const pending0 = cluster.map_shared_rank(&sm.pending[par], 0);
+        uint32_t lmin = 0xffffffffu;
         if (tid == 0) sm.nkeep = 0;
         __syncthreads();
-        // ---- scan: claim degree <= k (queued here), keep degree > k
+        // ---- scan: take degree <= k (queued here), keep degree > k; nothing changes a degree meanwhile
+        uint32_t lclaims = 0;
         for (uint32_t j0 = 0; j0 < nrem; j0 += kTailTB) {
             const uint32_t j = j0 + tid;
             bool keep = false;
             uint32_t li = 0;
             if (j < nrem) {
                 li = cur[j];
-                const bool taken = (*reinterpret_cast<volatile uint32_t*>(&sm.claim[li >> 5]) >> (li & 31u)) & 1u;
-                if (!taken) {
-                    const uint32_t d = *reinterpret_cast<volatile uint32_t*>(&sm.deg[li]);
+                const uint32_t bit = 1u << (li & 31u);
+                if (!(sm.taken[li >> 5] & bit)) {
+                    const uint32_t d = sm.deg[li];
                     if (d > k) {
                         keep = true;
                         lmin = min(lmin, d);
                     } else {
-                        const uint32_t bit = 1u << (li & 31u);
-                        const uint32_t i = li * C + rank;
-                        const uint64_t b0 = a.off[i], b1 = a.off[i + 1];
-                        if (!(atomicOr(&sm.claim[li >> 5], bit) & bit)) {
-                            ++lclaims;
-                            sm.q[atomicAdd(&sm.qtail, 1u)] = make_uint2((uint32_t)b0, (uint32_t)(b1 - b0));
-                        }
+                        atomicOr(&sm.taken[li >> 5], bit);
+                        prefetch_row(a.adj, sm.rbeg[li], sm.rlen[li]);
+                        sm.q[atomicAdd(&sm.qtail, 1u)] = (uint16_t)li;
+                        ++lclaims;
                     }
                 }
             }
             const uint32_t bal = __ballot_sync(kFullMask, keep);
             uint32_t base = 0;
-            if ((tid & 31u) == 0 && bal) base = atomicAdd(&sm.nkeep, (uint32_t)__popc(bal));
+            if (lane == 0 && bal) base = atomicAdd(&sm.nkeep, (uint32_t)__popc(bal));
             base = __shfl_sync(kFullMask, base, 0);
             if (keep) nxt[base + __popc(bal & lanemask_lt())] = (uint16_t)li;
         }
         if (tid == 0) scanned += nrem;
         {
-            // the scan's claims count as pending before this block's token is given back
             const uint32_t c = (uint32_t)block_sum<uint64_t>((uint64_t)lclaims, sm.red64);
-            if (tid == 0) atomicAdd(pending0, c - 1u);  // + claims - token
+            if (tid == 0 && c) atomicAdd(pending0, c);
         }
+        cluster.sync();  // every scan take is counted and every taken bit of the scan is set
+        // ---- the cluster's taken bits, for the drain's look-ups
+        for (uint32_t w = tid; w < C * wmax; w += kTailTB) {
+            const uint32_t b = w / wmax, ww = w - b * wmax;
+            sm.gone[b * kTailWPB + ww] =
+                *reinterpret_cast<volatile uint32_t*>(cluster.map_shared_rank(&sm.taken[ww], (int)b));
+        }
+        __syncthreads();
         stamp(11, global_ns());
-        // ---- drain: a neighbour above k loses one degree (Algorithm 2's
-        // drain reads it first; a neighbour at or below k is taken or being
-        // taken and is skipped); if a concurrent drain got it to k first, the
-        // decrement is undone; one brought to k is claimed and queued at its owner
-        auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
-            uint32_t d[kBatch], old[kBatch], live = 0;
+        // ---- drain: a neighbour not gone loses one degree at its owner; the one decrement
+        // that takes it from k + 1 to k queues it there; one that finds it at or below k
+        // (taken during this level) is undone
+        auto visit = [&](const uint32_t* u, uint32_t valid) {
+            uint32_t old[kBatch], live = 0;
             uint32_t* dp[kBatch];
 #pragma unroll
             for (uint32_t jj = 0; jj < kBatch; ++jj) {
                 dp[jj] = nullptr;
-                d[jj] = 0;
+                old[jj] = 0;
                 if (!(valid >> jj & 1u)) continue;
                 if (u[jj] >= r) {
                     bad = true;
                     continue;
                 }
-                dp[jj] = cluster.map_shared_rank(&sm.deg[u[jj] / C], (int)(u[jj] % C));
-                d[jj] = *reinterpret_cast<volatile uint32_t*>(dp[jj]);
+                const uint32_t ru = u[jj] % C, lu = u[jj] / C;
+                if (sm.gone[ru * kTailWPB + (lu >> 5)] >> (lu & 31u) & 1u) continue;
+                dp[jj] = cluster.map_shared_rank(&sm.deg[lu], (int)ru);
+                old[jj] = atomicSub(dp[jj], 1u);
+                ++natom;
+                live |= 1u << jj;
             }
-#pragma unroll
-            for (uint32_t jj = 0; jj < kBatch; ++jj) {
-                if (dp[jj] && d[jj] > k) {
-                    old[jj] = atomicSub(dp[jj], 1u);
-                    ++natom;
-                    live |= 1u << jj;
-                }
-            }
+            uint32_t claim = 0;
 #pragma unroll
             for (uint32_t jj = 0; jj < kBatch; ++jj) {
                 if (!(live >> jj & 1u)) continue;
                 if (old[jj] <= k) {
                     atomicAdd(dp[jj], 1u);
                     ++natom;
-                } else if (old[jj] - 1 == k) {
-                    const uint32_t uu = u[jj], lu = uu / C, ow = uu % C;
-                    uint32_t* cw = cluster.map_shared_rank(&sm.claim[lu >> 5], (int)ow);
-                    const uint32_t bit = 1u << (lu & 31u);
-                    const uint64_t b0 = a.off[uu], b1 = a.off[uu + 1];  // loaded alongside the claim
-                    if (!(atomicOr(cw, bit) & bit)) {
-                        ++lclaims;
-                        // pending up and a slot at the owner, both waited for before the slot is
-                        // written: the count never reads zero while u is claimed but not yet queued
-                        const uint32_t was = atomicAdd(pending0, 1u);
-                        const uint32_t slot = atomicAdd(cluster.map_shared_rank(&sm.qtail, (int)ow), 1u);
-                        if (was == 0xffffffffu || slot >= kTailVPC) {
-                            bad = true;
-                        } else {
-                            // one 8-byte store: the owner sees the slot empty or complete
-                            volatile unsigned long long* sp = reinterpret_cast<volatile unsigned long long*>(
-                                cluster.map_shared_rank(&sm.q[slot], (int)ow));
-                            *sp = ((unsigned long long)(uint32_t)(b1 - b0) << 32) | (uint32_t)b0;
-                        }
-                    }
+                } else if (old[jj] == k + 1) {
+                    claim |= 1u << jj;
                 } else {
                     lmin = min(lmin, old[jj] - 1);
                 }
             }
+            // the warp's takes: one pending increment by a leader, a slot at each owner and the
+            // row bounds there, then the row asked into L2 and the slot written (the count never
+            // reads zero while a take is unqueued)
+            const uint32_t wsum = warp_sum((uint32_t)__popc(claim));
+            if (wsum == 0) return;
+            uint32_t was = 0;
+            if (lane == 0) was = atomicAdd(pending0, wsum);
+            uint32_t slot[kBatch], rb[kBatch], rl[kBatch];
+#pragma unroll
+            for (uint32_t jj = 0; jj < kBatch; ++jj) {
+                if (!(claim >> jj & 1u)) continue;
+                const uint32_t ru = u[jj] % C, lu = u[jj] / C;
+                slot[jj] = atomicAdd(cluster.map_shared_rank(&sm.qtail, (int)ru), 1u);
+                rb[jj] = *cluster.map_shared_rank(&sm.rbeg[lu], (int)ru);
+                rl[jj] = *cluster.map_shared_rank(&sm.rlen[lu], (int)ru);
+            }
+#pragma unroll
+            for (uint32_t jj = 0; jj < kBatch; ++jj)
+                if (claim >> jj & 1u) prefetch_row(a.adj, rb[jj], rl[jj]);
+            was = __shfl_sync(kFullMask, was, 0);
+            if (was == 0xffffffffu) bad = true;
+#pragma unroll
+            for (uint32_t jj = 0; jj < kBatch; ++jj) {
+                if (!(claim >> jj & 1u)) continue;
+                if (slot[jj] >= kTailVPC) {
+                    bad = true;
+                    continue;
+                }
+                volatile uint16_t* sp = cluster.map_shared_rank(&sm.q[slot[jj]], (int)(u[jj] % C));
+                *sp = (uint16_t)(u[jj] / C);
+            }
         };
         // ---- drain this block's queue until the cluster has nothing pending
         uint32_t qhead = 0;
-        const uint64_t w0 = global_ns();
-        uint64_t wait_start = w0;
+        uint64_t wait_start = global_ns();
         for (;;) {
             if (tid == 0) {
-                const uint32_t t = *reinterpret_cast<volatile uint32_t*>(&sm.qtail);
-                uint32_t take = min(t - qhead, kTailTB);
-                sm.stop = 0;
-                if (take == 0) {
-                    // nothing queued here: the level is over once nothing is pending anywhere
-                    if (*reinterpret_cast<volatile uint32_t*>(pending0) == 0) sm.stop = 1;
-                    else if (global_ns() - wait_start > a.limit_ns) { sm.stop = 1; timeout = true; }
-                    else __nanosleep(64);
+                // wait here, alone, for queued work or the level's end: the queue tail is local and
+                // polled tightly, the cluster's pending count every few polls
+                uint32_t take = 0, stop = 0;
+                for (uint32_t spins = 0;; ++spins) {
+                    const uint32_t t = *reinterpret_cast<volatile uint32_t*>(&sm.qtail);
+                    if (t != qhead) {
+                        take = min(t - qhead, kTailTB);
+                        break;
+                    }
+                    if ((spins & 7u) == 7u) {
+                        if (*reinterpret_cast<volatile uint32_t*>(pending0) == 0) {
+                            // nothing queued here (re-read: a take may have landed meanwhile)
+                            if (*reinterpret_cast<volatile uint32_t*>(&sm.qtail) == qhead) {
+                                stop = 1;
+                                break;
+                            }
+                            continue;
+                        }
+                        if (global_ns() - wait_start > a.limit_ns) {
+                            stop = 1;
+                            timeout = true;
+                            break;
+                        }
+                    }
                 }
+                sm.stop = stop;
                 sm.batch_n = take;
             }
             __syncthreads();
             const uint32_t nb = sm.batch_n;
             if (sm.stop) break;
-            if (nb == 0) {
-                __syncthreads();
-                continue;
-            }
-            // the batch's rows: slots qhead .. qhead + nb, (row start, length) each, written by the
-            // claimer right after it reserved the slot (length first, start last): wait for it, bounded
-            uint32_t len = 0;
-            uint64_t bg = 0;
+            // the batch's vertices: slots qhead .. qhead + nb, each written by its taker right
+            // after it reserved the slot: wait for it, bounded
+            uint32_t len = 0, bg = 0;
             if (tid < nb) {
-                volatile unsigned long long* sl = reinterpret_cast<volatile unsigned long long*>(&sm.q[qhead + tid]);
-                unsigned long long x = *sl;
+                volatile uint16_t* sl = &sm.q[qhead + tid];
+                uint16_t x = *sl;
                 const uint64_t s0 = global_ns();
-                while ((uint32_t)x == kSlotEmpty) {
+                while (x == kSlotEmpty) {
                     if (global_ns() - s0 > a.limit_ns) { timeout = true; break; }
                     x = *sl;
                 }
-                if ((uint32_t)x != kSlotEmpty) {
-                    bg = (uint32_t)x;
-                    len = (uint32_t)(x >> 32);
+                if (x != kSlotEmpty && x < V) {
+                    atomicOr(&sm.taken[x >> 5], 1u << (x & 31u));
+                    bg = sm.rbeg[x];
+                    len = sm.rlen[x];
+                } else if (x != kSlotEmpty) {
+                    bad = true;
                 }
             }
             uint32_t total;
-            const uint32_t st = block_excl_scan<uint32_t>(len, sm.red, &total);
-            sm.start[tid] = st;
-            sm.beg[tid] = bg;
-            __syncthreads();
-            for (uint32_t e0 = tid; e0 < total; e0 += kBatch * kTailTB) {
-                uint32_t bu[kBatch], bv[kBatch], valid = 0;
+            if (nb == 1) {
+                // one row (the common case in the last levels): no scan
+                if (tid == 0) {
+                    sm.start[0] = 0;
+                    sm.beg[0] = bg;
+                    sm.batch_total = len;
+                }
+                __syncthreads();
+                total = sm.batch_total;
+            } else {
+                const uint32_t st = block_excl_scan<uint32_t>(len, sm.red, &total);
+                sm.start[tid] = st;
+                sm.beg[tid] = bg;
+                __syncthreads();
+            }
+            if (a.trace) {
+                stamp(15, global_ns());
+                stamp(16, ((uint64_t)nb << 32) | total);
+            }
+            for (uint32_t w0 = tid & ~31u; w0 < total; w0 += kBatch * kTailTB) {
+                uint32_t bu[kBatch], valid = 0;
 #pragma unroll
                 for (uint32_t j = 0; j < kBatch; ++j) {
-                    const uint32_t e = e0 + j * kTailTB;
+                    const uint32_t e = w0 + lane + j * kTailTB;
                     bu[j] = 0;
-                    bv[j] = 0;
                     if (e < total) {
                         uint32_t lo = 0, hi = nb;  // row = last whose start is <= e
                         while (hi - lo > 1) {
                             const uint32_t mid = (lo + hi) >> 1;
                             if (sm.start[mid] <= e) lo = mid; else hi = mid;
                         }
-                        bu[j] = ld_stream(a.adj + sm.beg[lo] + (e - sm.start[lo]));
+                        bu[j] = a.adj[sm.beg[lo] + (e - sm.start[lo])];
                         valid |= 1u << j;
                     }
                 }
-                visit(bu, bv, valid);
+                visit(bu, valid);
             }
-            __syncthreads();  // every drain of the batch (and the claims it made) is done
+            __syncthreads();  // every drain of the batch is done and its takes are counted
+            if (a.trace) stamp(17, global_ns());
             if (tid == 0) atomicSub(pending0, nb);
             qhead += nb;
             wait_start = global_ns();
         }
         stamp(12, global_ns());
         // ---- the level's totals over the cluster; queue slots back to empty for the next level
-        for (uint32_t i = tid; i < qhead; i += kTailTB) sm.q[i] = make_uint2(kSlotEmpty, 0u);
+        for (uint32_t i = tid; i < qhead; i += kTailTB) sm.q[i] = kSlotEmpty;
         lmin = block_min_u32(lmin, sm.red);
-        const uint64_t bc = block_sum<uint64_t>((uint64_t)lclaims, sm.red64);
         const uint32_t to = __syncthreads_or(timeout || bad);
         if (tid == 0) {
+            // (level parity: a block writes these again two levels on, after every block passed the
+            // next level's barriers and so has read them)
             sm.pub_min[par] = lmin;
-            sm.pub_claims[par] = (uint32_t)bc;
+            sm.pub_claims[par] = qhead;  // every vertex this block took at this level went through its queue
             sm.pub_err[par] = to;
             sm.qtail = 0;
-            // the next level's tokens: that count was last used at the previous level, which every
-            // block left before the previous barrier
-            if (rank == 0) sm.pending[par ^ 1u] = C;
         }
         nrem = sm.nkeep;
         cluster.sync();  // every block's drains of this level are done and its totals published
@@ -336,7 +412,7 @@ __global__ void __launch_bounds__(kTailTB, 1) kcore_tail_kernel(TailArgs a) {
     for (uint32_t li = tid; li < V; li += kTailTB) a.core[a.rid[li * C + rank]] = sm.deg[li];
     natom = warp_sum(natom);
     scanned = warp_sum(scanned);
-    if ((tid & 31u) == 0) {
+    if (lane == 0) {
         if (natom) atomicAdd(&a.stats->atomics, (unsigned long long)natom);
         if (scanned) atomicAdd(&a.stats->rem_scanned, (unsigned long long)scanned);
     }
@@ -494,8 +570,8 @@ dsg_status kcore_tail(uint32_t n, const uint64_t* off, const uint32_t* adj, uint
                                                                                     newid, coff, fill, cadj, cnt);
     }
     DSG_TRY_CUDA(cudaGetLastError());
-    if (ecount >= (uint64_t)kSlotEmpty) {
-        // row offsets do not fit the cluster's 32-bit queue slots: finish with the grid-wide
+    if (ecount >= (uint64_t)kOffMax) {
+        // row offsets do not fit the cluster's 32-bit row starts: finish with the grid-wide
         // kernel on the compacted graph instead, then put its core numbers in place
         uint32_t* ccore;
         DSG_TRY_CUDA(sc.get(&ccore, r));
@@ -526,7 +602,7 @@ dsg_status kcore_tail(uint32_t n, const uint64_t* off, const uint32_t* adj, uint
         return DSG_OK;
     }
     // ---- the cluster: 16 blocks (each holds at most kTailVPC vertices, so 16 always suffice)
-    const uint32_t C = 16;
+    const uint32_t C = kTailC;
     const size_t smem = sizeof(TailSmem);
     DSG_TRY_CUDA(cudaFuncSetAttribute(kcore_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (cudaFuncSetAttribute(kcore_tail_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {

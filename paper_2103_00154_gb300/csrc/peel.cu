@@ -4,22 +4,30 @@
 // Per round r, with S_r and E_r = |E(S_r)| known to every block:
 //   phase 1 (Algorithm 1's first part, over the active vertices): every alive vertex is
 //     tested against T_r = floor(2(p+q)E_r / (q|S_r|)), i.e. deg <= 2(1+eps)rho
-//     exactly; failures are marked and queued (short rows by vertex, long rows
-//     as chunk items), survivors are compacted into the next alive list
-//     (warp ballot + block scan + one atomic per block and list);
+//     exactly; failures are marked (state word and status map) and queued
+//     (short rows with their row bounds, long rows as chunk items), survivors
+//     are compacted into the next alive list (warp ballot + block scan + one
+//     atomic per block and list); the degrees of the failures are summed (X);
 //   grid barrier (Algorithm 1's synchronisation between its two parts);
 //   phase 2 (Alg. 1 part 2): every adjacency entry u of every failed v is read
-//     once; an alive u loses one degree (atomicSub) and the edge counts as
-//     removed; an edge whose both ends failed this round counts once (u > v);
-//     block-reduced removal counts go to one global counter (Algorithm 1's
-//     reduction of the removed edges);
-//   grid barrier; every block derives S_{r+1}, E_{r+1} from the monotone
-//   counters; block 0 records the history and keeps the densest set (strict
-//   ">": a later round replaces the best only when strictly denser, as in
-//   Algorithm 1).
+//     once; u's bits in the status map say whether it is still alive (and
+//     whether it is a hub); an alive u loses one degree (atomicSub, combined
+//     per block for hubs) and the decrement is counted (D);
+//   grid barrier; every block derives S_{r+1} and E_{r+1} from the monotone
+//     counters and keeps the densest set (strict ">": a later round replaces
+//     the best only when strictly denser, as in Algorithm 1); block 0 records
+//     the history.
+// The edges removed in round r (Algorithm 1's reduction) are (X + D) / 2: the
+// failures' degrees count every edge between two failures twice and every
+// edge from a failure to a survivor once, and D counts the latter once more.
+// So phase 2 never needs to tell a neighbour that failed in this round from
+// one that failed earlier, and reads only the status map (2 bits per vertex,
+// L2-resident) rather than the state words.
 //
 // Vertex state is one 32-bit word: an alive vertex holds its degree inside
 // S_r (< 2^31); a failed one holds 0x80000000 | (round it failed, 1-based).
+// Status map: word u / 16, bit 2 (u % 16) = u has failed, bit 2 (u % 16) + 1
+// = u is a hub (first-round degree at or above the hub threshold).
 #include <algorithm>
 #include <cstdlib>
 #include <string>
@@ -46,9 +54,9 @@ struct __align__(128) PeelCtl {
     unsigned long long pad4[15];
     unsigned long long surv;    // cursor of survivor writes (all rounds)
     unsigned long long pad5[15];
-    unsigned long long dE;      // sum of removed edges
+    unsigned long long xsum;    // sum over the rounds of the failures' degrees (X)
     unsigned long long pad6[15];
-    unsigned long long dec;     // alive-neighbour decrements
+    unsigned long long dec;     // alive-neighbour decrements (D)
     unsigned long long pad7[15];
     unsigned long long rounds, best_round, best_E, best_V;
     unsigned long long stamps;
@@ -65,7 +73,10 @@ struct PeelArgs {
     uint32_t* listA;
     uint32_t* listB;
     uint32_t* F;
+    uint64_t* FB;         // nullable: row start ...
+    uint32_t* FL;         // ... and length of each F entry (else read from off)
     uint64_t* C;
+    uint32_t* map;        // status map, (n + 15) / 16 words
     uint64_t* hist_S;
     uint64_t* hist_E;
     uint64_t hist_cap;
@@ -97,13 +108,24 @@ struct PeelSmem {
     AggTable agg;
     uint64_t bases[4];
     uint64_t red[33];
+    uint32_t surv_at[4][TB / 32];  // a tile's survivors per (slice, warp), then their exclusive prefix in id order
 };
+
+// Bits 0..15 of x spread to the even positions 0, 2, ..., 30.
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
 
 template <int TB>
 __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a) {
     __shared__ PeelSmem<TB> sm;
     PeelCtl* ctl = a.ctl;
-    const uint32_t tid = threadIdx.x;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
     const bool resume = a.r0 > 0;
     uint64_t S = resume ? a.S0 : a.n, E = resume ? a.E0 : a.m;
     uint64_t r = a.r0;
@@ -128,62 +150,153 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         const uint32_t T = peel_threshold(a.p, a.q, E, S);
         const uint32_t mark = kDead | (uint32_t)(r + 1);
         // ------------------------------------------------ phase 1: test + compact
+        // the first round of a launch walks vertex ids in order (every vertex, or
+        // every vertex a resumed peel has not failed yet) and writes the status map
+        // whole, two words per warp; later rounds walk the alive list and set the
+        // failures' bits
         const bool fresh = r == 0;                  // identity list, degrees from the rows
         const bool scan_all = !alive && resume;     // a resumed peel's first round: every vertex, failed ones skipped
+        const bool by_id = fresh || scan_all;
         const uint64_t span = scan_all ? a.n : S;
-        for (uint64_t t = (uint64_t)blockIdx.x * TB; t < span; t += (uint64_t)gridDim.x * TB) {
-            uint64_t i = t + tid;
-            bool valid = i < span;
-            uint32_t v = 0, d = 0, nch = 0;
-            uint64_t len = 0;
-            bool fail = false;
-            if (valid) {
-                if (fresh) {
-                    v = (uint32_t)i;
-                    len = a.off[v + 1] - a.off[v];
-                    d = (uint32_t)len;
-                } else if (scan_all) {
-                    v = (uint32_t)i;
-                    d = a.st[v];
-                    valid = !(d & kDead);
-                } else {
-                    v = alive[i];
-                    d = a.st[v];
+        // a tile is `items` slices of TB: thread tid takes i = t + j TB + tid for
+        // j < items (4 in the by-id rounds, whose tiles would otherwise be
+        // short; 1 on the alive list); the first pass tests and marks, the
+        // second writes the lists at the tile's reserved places
+        const uint32_t items = by_id ? 4u : 1u;
+        uint64_t X = 0;
+        for (uint64_t t = (uint64_t)blockIdx.x * TB * items; t < span; t += (uint64_t)gridDim.x * TB * items) {
+            uint32_t fail_m = 0, short_m = 0, surv_m = 0, nch_sum = 0;
+            for (uint32_t j = 0; j < items; ++j) {
+                const uint64_t i = t + (uint64_t)j * TB + tid;
+                bool valid = i < span;
+                bool gone = false;  // failed in an earlier round (resumed first round)
+                uint32_t v = 0, d = 0;
+                uint64_t len = 0;
+                bool fail = false;
+                if (valid) {
+                    if (by_id) {
+                        v = (uint32_t)i;
+                        len = a.off[v + 1] - a.off[v];
+                        if (fresh) {
+                            d = (uint32_t)len;
+                        } else {
+                            d = a.st[v];
+                            gone = (d & kDead) != 0;
+                        }
+                    } else {
+                        v = alive[i];
+                        d = a.st[v];
+                    }
+                }
+                const bool hub = by_id && valid && len >= hot;
+                if (valid && !gone) {
+                    fail = d <= T;
+                    if (fail) {
+                        if (!by_id) len = a.off[v + 1] - a.off[v];
+                        a.st[v] = mark;
+                        X += d;
+                        if (len > a.short_max) {
+                            nch_sum += (uint32_t)((len + a.chunk_len - 1) / a.chunk_len);
+                        } else {
+                            short_m |= 1u << j;
+                        }
+                        fail_m |= 1u << j;
+                        if (!by_id) atomicOr(&a.map[v >> 4], 1u << (2u * (v & 15u)));
+                    } else {
+                        surv_m |= 1u << j;
+                        if (fresh) a.st[v] = d;
+                    }
+                }
+                if (by_id) {
+                    // each warp holds 32 consecutive ids starting at a multiple of 32
+                    const uint32_t bd = __ballot_sync(kFullMask, fail || gone);
+                    const uint32_t bh = __ballot_sync(kFullMask, hub);
+                    const uint64_t i0 = t + (uint64_t)j * TB + (tid & ~31u);
+                    if (lane == 0 && i0 < a.n) a.map[i0 >> 4] = spread16(bd) | (spread16(bh) << 1);
+                    if (lane == 16 && i0 + 16 < a.n)
+                        a.map[(i0 >> 4) + 1] = spread16(bd >> 16) | (spread16(bh >> 16) << 1);
                 }
             }
-            if (valid) {
-                fail = d <= T;
-                if (fail) {
-                    if (!fresh) len = a.off[v + 1] - a.off[v];
-                    a.st[v] = mark;
-                    if (len > a.short_max) nch = (uint32_t)((len + a.chunk_len - 1) / a.chunk_len);
-                } else if (fresh) {
-                    a.st[v] = d;
-                }
+            // survivors go to the next list in id order within the tile (slice, then
+            // warp, then lane), so the next round reads the states in order
+            for (uint32_t j = 0; j < items; ++j) {
+                const uint32_t c = __popc(__ballot_sync(kFullMask, surv_m >> j & 1u));
+                if (lane == 0) sm.surv_at[j][tid >> 5] = c;
             }
-            bool is_short = fail && nch == 0;
-            bool is_surv = valid && !fail;
-            // packed counts: short | surv << 16 | long-fail << 32
-            uint64_t pk = (uint64_t)is_short | ((uint64_t)is_surv << 16) | ((uint64_t)(nch > 0) << 32);
+            const uint32_t ns_t = __popc(short_m), nl_t = __popc(fail_m) - ns_t;
+            // packed counts: short | long-fail << 32 (at most 4 TB of each per tile)
+            uint64_t pk = (uint64_t)ns_t | ((uint64_t)nl_t << 32);
             uint64_t pk_tot;
             uint64_t pk_pre = block_excl_scan<uint64_t>(pk, sm.tile.scan_tmp64, &pk_tot);
             uint32_t ch_tot;
-            uint32_t ch_pre = block_excl_scan<uint32_t>(nch, sm.tile.scan_tmp, &ch_tot);
+            uint32_t ch_pre = block_excl_scan<uint32_t>(nch_sum, sm.tile.scan_tmp, &ch_tot);
+            uint64_t nv = 0;
+            if (tid < 32) {
+                // exclusive prefix of the (slice, warp) survivor counts, slice-major
+                constexpr uint32_t kW = TB / 32;
+                const uint32_t per = (items * kW + 31) / 32;  // counts per lane, consecutive
+                uint32_t loc[4], sum = 0;
+                for (uint32_t q = 0; q < per; ++q) {
+                    const uint32_t idx = tid * per + q;
+                    loc[q] = idx < items * kW ? sm.surv_at[idx / kW][idx % kW] : 0u;
+                    sum += loc[q];
+                }
+                const uint32_t inc = warp_incl_scan(sum);
+                nv = __shfl_sync(kFullMask, inc, 31);
+                uint32_t run = inc - sum;
+                for (uint32_t q = 0; q < per; ++q) {
+                    const uint32_t idx = tid * per + q;
+                    if (idx < items * kW) sm.surv_at[idx / kW][idx % kW] = run;
+                    run += loc[q];
+                }
+            }
             if (tid == 0) {
-                uint64_t ns = pk_tot & 0xffff, nv = (pk_tot >> 16) & 0xffff, nl = (pk_tot >> 32) & 0xffff;
+                uint64_t ns = pk_tot & 0xffff, nl = (pk_tot >> 32) & 0xffff;
                 sm.bases[0] = ns ? atomicAdd(&ctl->nshort, ns) : 0;
                 sm.bases[1] = nv ? atomicAdd(&ctl->surv, nv) : 0;
                 sm.bases[2] = ch_tot ? atomicAdd(&ctl->nchunk, (unsigned long long)ch_tot) : 0;
                 if (ns + nl) atomicAdd(&ctl->failed, ns + nl);
             }
             __syncthreads();
-            if (is_short) a.F[sm.bases[0] + (pk_pre & 0xffff)] = v;
-            if (is_surv) next[sm.bases[1] - surv_base + ((pk_pre >> 16) & 0xffff)] = v;
-            if (nch) {
-                uint64_t c0 = sm.bases[2] + ch_pre;
-                for (uint32_t c = 0; c < nch; ++c) a.C[c0 + c] = ((uint64_t)v << 32) | c;
+            uint64_t at_s = sm.bases[0] + (pk_pre & 0xffff);
+            const uint64_t v0 = sm.bases[1] - surv_base;
+            uint64_t at_c = sm.bases[2] + ch_pre;
+            for (uint32_t j = 0; j < items; ++j) {
+                const uint64_t i = t + (uint64_t)j * TB + tid;
+                uint32_t v = 0, nch = 0;
+                if ((fail_m | surv_m) >> j & 1u) v = by_id ? (uint32_t)i : alive[i];
+                if (short_m >> j & 1u) {
+                    a.F[at_s] = v;
+                    if (a.FB) {
+                        const uint64_t b0 = a.off[v];
+                        a.FB[at_s] = b0;
+                        a.FL[at_s] = (uint32_t)(a.off[v + 1] - b0);
+                    }
+                    ++at_s;
+                } else if (fail_m >> j & 1u) {
+                    const uint64_t len = a.off[v + 1] - a.off[v];
+                    nch = (uint32_t)((len + a.chunk_len - 1) / a.chunk_len);
+                }
+                {
+                    const uint32_t sb = __ballot_sync(kFullMask, surv_m >> j & 1u);
+                    if (surv_m >> j & 1u) next[v0 + sm.surv_at[j][tid >> 5] + __popc(sb & lanemask_lt())] = v;
+                }
+                // chunk items of the warp's long failures, written by the whole warp
+                // (a hub has hundreds of them)
+                for (uint32_t pend = __ballot_sync(kFullMask, nch != 0); pend; pend &= pend - 1) {
+                    const uint32_t src = __ffs(pend) - 1;
+                    const uint32_t cn = __shfl_sync(kFullMask, nch, src);
+                    const uint32_t cv = __shfl_sync(kFullMask, v, src);
+                    const uint64_t c0 = __shfl_sync(kFullMask, at_c, src);
+                    for (uint32_t c = lane; c < cn; c += 32) a.C[c0 + c] = ((uint64_t)cv << 32) | c;
+                }
+                at_c += nch;
             }
             __syncthreads();
+        }
+        {
+            const uint64_t bx = block_sum<uint64_t>(X, sm.red);
+            if (tid == 0 && bx) atomicAdd(&ctl->xsum, (unsigned long long)bx);
         }
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
         stamp();
@@ -191,31 +304,31 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         const uint64_t short_hi = ld_relaxed_u64(&ctl->nshort);
         const uint64_t chunk_hi = ld_relaxed_u64(&ctl->nchunk);
         // ------------------------------------------------ phase 2: neighbour scan
-        uint64_t dE = 0, ndec = 0;
+        uint64_t ndec = 0;
         uint32_t* st = a.st;
-        auto visit = [&](const uint32_t* u, const uint32_t* v, uint32_t valid) {
+        const uint32_t* map = a.map;
+        auto visit = [&](const uint32_t* u, const uint32_t*, uint32_t valid) {
             uint32_t w[kBatch];
 #pragma unroll
             for (uint32_t j = 0; j < kBatch; ++j) {
 #ifdef DSG_DEBUG_BOUNDS
                 if ((valid >> j & 1u) && u[j] >= a.n) { atomicOr(&ctl->err, ERR_RANGE); valid &= ~(1u << j); }
 #endif
-                w[j] = (valid >> j & 1u) ? st[u[j]] : kDead;
+                w[j] = (valid >> j & 1u) ? map[u[j] >> 4] : 1u;
             }
 #pragma unroll
             for (uint32_t j = 0; j < kBatch; ++j) {
                 if (!(valid >> j & 1u)) continue;
-                if (!(w[j] & kDead)) {
-                    // w is u's degree at the start of the round (or lower): a
-                    // high one marks a hub, whose decrements are combined per block
-                    if (w[j] < hot || !agg_add(sm.agg, u[j])) atomicSub(&st[u[j]], 1u);
+                const uint32_t b = w[j] >> (2u * (u[j] & 15u));
+                if (!(b & 1u)) {
+                    // alive: one degree less (hubs' decrements combined in the block)
+                    if (!(b & 2u) || !agg_add(sm.agg, u[j])) atomicSub(&st[u[j]], 1u);
                     ++ndec;
-                } else if (w[j] == mark && u[j] > v[j]) {
-                    ++dE;
                 }
             }
         };
-        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n);
+        scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n,
+                          a.FB, a.FL);
         // flush the combined hub decrements (block_sum below synchronises first)
         __syncthreads();
         for (uint32_t i = tid; i < kAggSlots; i += TB) {
@@ -226,15 +339,14 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                 sm.agg.cnt[i] = 0;
             }
         }
-        uint64_t bdec = block_sum<uint64_t>(ndec, sm.red);
-        uint64_t bdE = block_sum<uint64_t>(dE, sm.red) + bdec;
-        if (tid == 0 && bdE) atomicAdd(&ctl->dE, (unsigned long long)bdE);
+        const uint64_t bdec = block_sum<uint64_t>(ndec, sm.red);
         if (tid == 0 && bdec) atomicAdd(&ctl->dec, (unsigned long long)bdec);
         if (!grid_barrier(&ctl->bar, &ctl->err, a.limit_ns)) return;
         stamp();
-        const uint64_t dE_tot = ld_relaxed_u64(&ctl->dE);
+        // edges removed so far: (X + D) / 2 summed over the rounds
+        const uint64_t removed = (ld_relaxed_u64(&ctl->xsum) + ld_relaxed_u64(&ctl->dec)) / 2;
         const uint64_t S1 = (uint64_t)a.n - failed_hi;
-        const uint64_t E1 = a.m - dE_tot;
+        const uint64_t E1 = a.m - removed;
         ++r;
         if (blockIdx.x == 0 && tid == 0) {
             if (r < a.hist_cap) {
@@ -359,7 +471,10 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
     DSG_TRY_CUDA(sc.get(&a.listA, n));
     DSG_TRY_CUDA(sc.get(&a.listB, n));
     DSG_TRY_CUDA(sc.get(&a.F, n));
+    DSG_TRY_CUDA(sc.get(&a.FB, n));
+    DSG_TRY_CUDA(sc.get(&a.FL, n));
     DSG_TRY_CUDA(sc.get(&a.C, chunk_cap));
+    DSG_TRY_CUDA(sc.get(&a.map, ((size_t)n + 15) / 16));
     DSG_TRY_CUDA(sc.get(&a.hist_S, cap));
     DSG_TRY_CUDA(sc.get(&a.hist_E, cap));
     DSG_TRY_CUDA(sc.get(&a.ctl, 1));
@@ -695,7 +810,8 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     const size_t b_chunk = align256((size_t)chunk_cap * 8);
     const size_t b_hist = align256((size_t)cap * 8);
     const size_t b_ctl = align256(sizeof(PeelCtl));
-    const size_t need = 4 * b_list + b_chunk + 2 * b_hist + b_ctl;
+    const size_t b_map = align256(((size_t)n + 15) / 16 * 4);
+    const size_t need = 4 * b_list + b_chunk + b_map + 2 * b_hist + b_ctl;
     if (need > kNoAllocScratchBytes) {
         set_error("bahmani_noalloc: this graph needs %zu bytes of scratch, above the fixed %zu-byte buffer "
                   "(use dsg_bahmani)", need, (size_t)kNoAllocScratchBytes);
@@ -716,7 +832,10 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     a.listA = reinterpret_cast<uint32_t*>(base + o); o += b_list;
     a.listB = reinterpret_cast<uint32_t*>(base + o); o += b_list;
     a.F = reinterpret_cast<uint32_t*>(base + o); o += b_list;
+    a.FB = nullptr;  // short rows' bounds are read from off
+    a.FL = nullptr;
     a.C = reinterpret_cast<uint64_t*>(base + o); o += b_chunk;
+    a.map = reinterpret_cast<uint32_t*>(base + o); o += b_map;
     a.hist_S = reinterpret_cast<uint64_t*>(base + o); o += b_hist;
     a.hist_E = reinterpret_cast<uint64_t*>(base + o); o += b_hist;
     a.ctl = reinterpret_cast<PeelCtl*>(base + o);
@@ -772,8 +891,8 @@ struct dsg_peel_state {
     uint64_t r = 0, S = 0, E = 0, best_round = 0, best_E = 0, best_V = 0, cap = 0, chunk_cap = 0;
     bool done = false;
     dsg::Tuning tu;
-    uint32_t *st = nullptr, *listA = nullptr, *listB = nullptr, *F = nullptr;
-    uint64_t *C = nullptr, *hist_S = nullptr, *hist_E = nullptr;
+    uint32_t *st = nullptr, *listA = nullptr, *listB = nullptr, *F = nullptr, *FL = nullptr, *map = nullptr;
+    uint64_t *FB = nullptr, *C = nullptr, *hist_S = nullptr, *hist_E = nullptr;
     dsg::PeelCtl* ctl = nullptr;
 };
 
@@ -785,7 +904,8 @@ static constexpr uint64_t kSnapHeaderWords = 16;
 static void peel_state_release(dsg_peel_state* ps) {
     if (!ps) return;
     cudaStream_t s = ps->g ? ps->g->stream : nullptr;
-    void* bufs[] = {ps->st, ps->listA, ps->listB, ps->F, ps->C, ps->hist_S, ps->hist_E, ps->ctl};
+    void* bufs[] = {ps->st, ps->listA, ps->listB, ps->F, ps->FB, ps->FL, ps->C, ps->map, ps->hist_S, ps->hist_E,
+                    ps->ctl};
     for (void* b : bufs)
         if (b) dev_free(b, s);
     if (s) cudaStreamSynchronize(s);
@@ -814,7 +934,10 @@ static dsg_status peel_state_new(const dsg_graph* g, uint32_t p, uint32_t q, dsg
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->listA, nb, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->listB, nb, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->F, nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->FB, 2 * nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->FL, nb, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->C, ps->chunk_cap * 8, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->map, (((size_t)(n ? n : 1) + 15) / 16 * 4 + 255) & ~size_t(255), s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->hist_S, ps->cap * 8, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->hist_E, ps->cap * 8, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->ctl, sizeof(PeelCtl), s);
@@ -843,7 +966,10 @@ static dsg_status peel_state_run(dsg_peel_state* ps, uint64_t max_rounds) {
     a.listA = ps->listA;
     a.listB = ps->listB;
     a.F = ps->F;
+    a.FB = ps->FB;
+    a.FL = ps->FL;
     a.C = ps->C;
+    a.map = ps->map;
     a.hist_S = ps->hist_S;
     a.hist_E = ps->hist_E;
     a.hist_cap = ps->cap;
@@ -864,7 +990,7 @@ static dsg_status peel_state_run(dsg_peel_state* ps, uint64_t max_rounds) {
     PeelCtl init;
     memset(&init, 0, sizeof(init));
     init.failed = (uint64_t)g->n - ps->S;  // the counters the kernel derives S and E from
-    init.dE = g->m - ps->E;
+    init.xsum = 2 * (g->m - ps->E);
     DSG_TRY_CUDA(cudaMemcpyAsync(ps->ctl, &init, sizeof(PeelCtl), cudaMemcpyHostToDevice, s));
     cudaError_t e;
     switch (ps->tu.block) {

@@ -222,6 +222,27 @@ def test_star_hubs_straddle_thresholds():
         check_peel(g, c, *pq, tag="stars")
 
 
+def test_giant_rows_split_or_skewed():
+    # rows above 8192 raw entries are cut into value ranges by splitters from
+    # a sample of the row; a row whose values are mostly one repeated id makes
+    # a range above 8192 entries and takes the radix path instead; rows of
+    # distinct ids spread evenly, or crowded into a narrow band of ids
+    n = 200_000
+    rng = np.random.default_rng(41)
+    pairs = [np.stack([np.zeros(15000, np.uint32), np.ones(15000, np.uint32)], 1),       # one id 15000 times
+             np.stack([np.zeros(6000, np.uint32), rng.integers(2, n, 6000, dtype=np.uint32)], 1),
+             np.stack([np.full(40000, 7, np.uint32), rng.integers(0, n, 40000, dtype=np.uint32)], 1),  # spread
+             np.stack([np.full(30000, 9, np.uint32), rng.integers(1000, 1400, 30000, dtype=np.uint32)], 1),  # band
+             np.stack([np.full(9000, 11, np.uint32), np.arange(20000, 29000, dtype=np.uint32)], 1)]      # sorted run
+    arr = np.concatenate(pairs)
+    raw = inputs.RawGraph(n, arr[:, 0].copy(), arr[:, 1].copy(), "giant rows")
+    c = oracle.from_raw(raw)
+    g = gpu_graph(raw)
+    check_csr(g, c)
+    check_core(g, c)
+    check_peel(g, c, 1, 10, tag="giant rows")
+
+
 def test_long_paths_and_chains():
     # many-sub-round drains: long paths, a ladder and a caterpillar
     raw = inputs.union(inputs.path(5000),
@@ -289,6 +310,22 @@ def test_core_numbers_do_not_depend_on_where_rows_are_drained(inline_max, local_
         c = oracle.from_raw(raw)
         dsg.set_tuning(inline_max=inline_max, local_work=local_work)
         check_core(gpu_graph(raw), c, f"inline {inline_max}/{local_work}")
+
+
+@pytest.mark.parametrize("tail", [0, 1, 64, 4096, 131072])
+def test_core_numbers_do_not_depend_on_where_the_cluster_takes_over(tail):
+    # the grid-wide levels hand the remaining graph to the one-cluster tail
+    # after the first level with at most `tail` vertices left (0: never):
+    # hub-heavy, planted-block and chain graphs, the largest with more
+    # remaining vertices than half the cluster's capacity, give the same core
+    # numbers wherever the hand-over happens
+    graphs = (inputs.chung_lu(n=1 << 17, m_draws=1 << 20, gamma=2.1, mean=16.0, wmax=8000.0, seed=21),
+              inputs.union(inputs.rmat(scale=14, m=1 << 18, seed=22), inputs.block(1 << 14, 300, 0.6, 22)),
+              inputs.union(inputs.path(5000), inputs.complete(90)))
+    for raw in graphs:
+        c = oracle.from_raw(raw)
+        dsg.set_tuning(kcore_tail=tail)
+        check_core(gpu_graph(raw), c, f"tail {tail}")
 
 
 def test_from_csr_paths():
