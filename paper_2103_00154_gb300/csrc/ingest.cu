@@ -986,11 +986,17 @@ __global__ void __launch_bounds__(256) giant_split_kernel(const uint32_t* __rest
         __syncthreads();
         const uint32_t nsp = sm.nsp;
         // ---- entries per range
-        for (uint32_t i0 = 0; i0 < L; i0 += 256) {
-            const uint32_t i = i0 + tid;
-            const uint32_t rg = i < L ? split_range(sm.spl, nsp, A[i]) : kSplitMaxRanges;
-            const uint32_t peers = __match_any_sync(kFullMask, rg);
-            if (rg < kSplitMaxRanges && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sm.rcnt[rg], (uint32_t)__popc(peers));
+        for (uint32_t i0 = 0; i0 < L; i0 += 4 * 256) {
+            uint32_t x[4];
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) x[j] = i0 + j * 256 + tid < L ? A[i0 + j * 256 + tid] : 0u;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                const uint32_t rg = i0 + j * 256 + tid < L ? split_range(sm.spl, nsp, x[j]) : kSplitMaxRanges;
+                const uint32_t peers = __match_any_sync(kFullMask, rg);
+                if (rg < kSplitMaxRanges && lane == (uint32_t)(__ffs(peers) - 1))
+                    atomicAdd(&sm.rcnt[rg], (uint32_t)__popc(peers));
+            }
         }
         __syncthreads();
         if (w == 0) {
@@ -1010,16 +1016,20 @@ __global__ void __launch_bounds__(256) giant_split_kernel(const uint32_t* __rest
             continue;
         }
         // ---- scatter by range (order inside a range does not matter: it is sorted next)
-        for (uint32_t i0 = 0; i0 < L; i0 += 256) {
-            const uint32_t i = i0 + tid;
-            const uint32_t x = i < L ? A[i] : 0u;
-            const uint32_t rg = i < L ? split_range(sm.spl, nsp, x) : kSplitMaxRanges;
-            const uint32_t peers = __match_any_sync(kFullMask, rg);
-            const uint32_t leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if (rg < kSplitMaxRanges && lane == leader) base = atomicAdd(&sm.rcur[rg], (uint32_t)__popc(peers));
-            base = __shfl_sync(kFullMask, base, leader);
-            if (rg < kSplitMaxRanges) B[sm.rstart[rg] + base + __popc(peers & lanemask_lt())] = x;
+        for (uint32_t i0 = 0; i0 < L; i0 += 4 * 256) {
+            uint32_t x[4];
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) x[j] = i0 + j * 256 + tid < L ? A[i0 + j * 256 + tid] : 0u;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                const uint32_t rg = i0 + j * 256 + tid < L ? split_range(sm.spl, nsp, x[j]) : kSplitMaxRanges;
+                const uint32_t peers = __match_any_sync(kFullMask, rg);
+                const uint32_t leader = __ffs(peers) - 1;
+                uint32_t base = 0;
+                if (rg < kSplitMaxRanges && lane == leader) base = atomicAdd(&sm.rcur[rg], (uint32_t)__popc(peers));
+                base = __shfl_sync(kFullMask, base, leader);
+                if (rg < kSplitMaxRanges) B[sm.rstart[rg] + base + __popc(peers & lanemask_lt())] = x[j];
+            }
         }
         __syncthreads();
         // ---- each range sorted and de-duplicated in place

@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         uint64_t X = 0;
         for (uint64_t t = (uint64_t)blockIdx.x * TB * items; t < span; t += (uint64_t)gridDim.x * TB * items) {
             uint32_t fail_m = 0, short_m = 0, surv_m = 0, nch_sum = 0;
+            uint64_t c_beg = 0, c_len = 0;  // the alive-list rounds' one item: its row, for the second pass
             for (uint32_t j = 0; j < items; ++j) {
                 const uint64_t i = t + (uint64_t)j * TB + tid;
                 bool valid = i < span;
@@ -192,7 +193,11 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                 if (valid && !gone) {
                     fail = d <= T;
                     if (fail) {
-                        if (!by_id) len = a.off[v + 1] - a.off[v];
+                        if (!by_id) {
+                            c_beg = a.off[v];
+                            len = a.off[v + 1] - c_beg;
+                            c_len = len;
+                        }
                         a.st[v] = mark;
                         X += d;
                         if (len > a.short_max) {
@@ -268,13 +273,13 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                 if (short_m >> j & 1u) {
                     a.F[at_s] = v;
                     if (a.FB) {
-                        const uint64_t b0 = a.off[v];
+                        const uint64_t b0 = by_id ? a.off[v] : c_beg;
                         a.FB[at_s] = b0;
-                        a.FL[at_s] = (uint32_t)(a.off[v + 1] - b0);
+                        a.FL[at_s] = (uint32_t)(by_id ? a.off[v + 1] - b0 : c_len);
                     }
                     ++at_s;
                 } else if (fail_m >> j & 1u) {
-                    const uint64_t len = a.off[v + 1] - a.off[v];
+                    const uint64_t len = by_id ? a.off[v + 1] - a.off[v] : c_len;
                     nch = (uint32_t)((len + a.chunk_len - 1) / a.chunk_len);
                 }
                 {

@@ -15,18 +15,19 @@ def test_code_hash_ignores_comments_but_not_code():
 
 
 def test_traffic_is_dropped_once_the_kernel_code_changes(tmp_path, monkeypatch):
-    files = {"kcore.cu": b"__global__ void k() {}  // v1\n", "dsg_kernels.cuh": b"", "dsg_common.cuh": b""}
-    sha = bench.kernel_source_sha("kcore_levels", read=lambda f: files[f])
+    files = {"kcore.cu": b"__global__ void k() {}  // v1\n", "kcore_tail.cu": b"", "dsg_kernels.cuh": b"",
+             "dsg_common.cuh": b""}
+    sha = bench.kernel_source_sha("kcore", read=lambda f: files[f])
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(
-        {"w": {"kcore_levels": {"bytes": 123, "source_sha": sha, "capture": "test"}}}))
+        {"w": {"kcore": {"bytes": 123, "source_sha": sha, "capture": "test"}}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_sha", lambda name, read=None: sha)
-    assert bench.dram_traffic("w", "kcore_levels") == 123
+    assert bench.dram_traffic("w", "kcore") == 123
     assert bench.dram_traffic("w", "peel_rounds") is None
-    assert bench.dram_traffic("other", "kcore_levels") is None
+    assert bench.dram_traffic("other", "kcore") is None
     monkeypatch.setattr(bench, "kernel_source_sha", lambda name, read=None: "0" * 16)
-    assert bench.dram_traffic("w", "kcore_levels") is None
+    assert bench.dram_traffic("w", "kcore") is None
 
 
 def test_kcore_byte_model_follows_the_method():
@@ -102,9 +103,11 @@ def test_replica_launch_runs_ranks_that_see_the_world(tmp_path):
     import subprocess
     import sys
     probe = tmp_path / "probe.py"
-    probe.write_text("import os, torch.distributed as d\n"
+    # each rank writes its own file: prints of two processes on one pipe can interleave
+    probe.write_text("import os, sys, torch.distributed as d\n"
                      "d.init_process_group('gloo')\n"
-                     "print('rank', d.get_rank(), 'of', d.get_world_size(), flush=True)\n"
+                     "with open(os.path.join(sys.argv[-1], 'rank%d' % d.get_rank()), 'w') as f:\n"
+                     "    f.write('rank %d of %d' % (d.get_rank(), d.get_world_size()))\n"
                      "d.destroy_process_group()\n")
     import socket
     with socket.socket() as sk:
@@ -114,6 +117,8 @@ def test_replica_launch_runs_ranks_that_see_the_world(tmp_path):
     at = [i for i, c in enumerate(cmd) if c.endswith("bench.py")]
     assert len(at) == 1
     cmd[at[0]] = str(probe)
+    cmd.append(str(tmp_path))
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=240)
     assert out.returncode == 0, out.stderr[-2000:]
-    assert "rank 0 of 2" in out.stdout and "rank 1 of 2" in out.stdout
+    assert (tmp_path / "rank0").read_text() == "rank 0 of 2"
+    assert (tmp_path / "rank1").read_text() == "rank 1 of 2"
