@@ -226,3 +226,29 @@ def random_small(n: int, p: float, seed: int) -> RawGraph:
     iu, ju = np.triu_indices(n, 1)
     keep = rng.random(iu.shape[0]) < p
     return RawGraph(n, iu[keep].astype(np.uint32), ju[keep].astype(np.uint32), f"gnp({n},{p},{seed})")
+
+
+def onion(n: int = 1 << 20, d: int = 64, core: int = 160) -> RawGraph:
+    """Nested shells around a clique: shell 0 is K_core; every vertex of shell
+    i >= 1 has d edges into shell i - 1, spread evenly (vertex j of the shell
+    to vertices (j d + t) mod |shell i-1|, t < d), and each shell is
+    ceil((d+1)/d) times the one inside it, so every inner vertex gets at
+    least d + 1 edges from outside.  Shells are added until at least n
+    vertices exist.  Deterministic (no seed).  With eps < 1/(2d) a round of
+    the (2+2eps) peel removes exactly the outermost shell (degree d, while
+    every vertex inside has at least 2d + 1 until its outer shell is gone),
+    so the peel takes about one round per shell: a long tail of rounds that
+    each remove a few percent of the survivors."""
+    sizes = [core]
+    while sum(sizes) < n:
+        sizes.append(-(-sizes[-1] * (d + 1) // d))
+    base = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    iu, ju = np.triu_indices(core, 1)
+    src, dst = [iu.astype(np.uint32)], [ju.astype(np.uint32)]
+    for i in range(1, len(sizes)):
+        j = np.repeat(np.arange(sizes[i], dtype=np.int64), d)
+        t = np.tile(np.arange(d, dtype=np.int64), sizes[i])
+        src.append((base[i] + j).astype(np.uint32))
+        dst.append((base[i - 1] + (j * d + t) % sizes[i - 1]).astype(np.uint32))
+    return RawGraph(int(base[-1]), np.concatenate(src), np.concatenate(dst),
+                    f"onion(n={n},d={d},core={core},shells={len(sizes)})")
