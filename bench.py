@@ -62,6 +62,12 @@ WORKLOADS = {
              "batch workload with n log-uniform in [1,000, 2,000,000]; each request asks for Bahmani at eps "
              "1/100 or 1/10 and, with probability 1/2, core numbers; admitted by free HBM, continuous batching",
         kind="serve", eps=[(1, 100), (1, 10)]),
+    "onion20": dict(
+        desc="nested shells around K_80: every vertex of shell i has 32 edges into shell i-1, each shell "
+             "33/32 times the one inside it, 1,078,301 vertices in 191 shells (a long thin tail: one shell "
+             "per round); Bahmani eps=1/1000 + core numbers",
+        gen=lambda: inputs.onion(n=1 << 20, d=32, core=80),
+        eps=[(1, 1000)], lazy_compare=True),
     "cl24": dict(
         desc="Chung-Lu n=16,777,216, exponent 2.1, mean degree 32, max expected degree 100,000, seed 2, "
              "2^28 generated pairs; Bahmani eps=1/10 + core numbers",
@@ -235,14 +241,14 @@ def kcore_bytes(n: int, m: int, st: dict, sum_core: int) -> int:
 
 def kcore_overhead_bytes(n: int, m: int, st: dict, sum_core: int) -> dict:
     """Traffic the kernel's schedule adds beyond kcore_bytes: the claim
-    bitmap (clear n/8, a claim word read per scanned vertex, one claim
-    atomic per vertex), the remaining-list writes, and the atomics above the
-    method's count (the kernel decrements every neighbour first and undoes
-    the decrement below the level, instead of reading first)."""
+    bitmap (clear n/8, at most a claim word read per scanned vertex, one
+    claim atomic per vertex), the remaining-list writes, and the atomics
+    above the method's count (a neighbour taken during the level is
+    decremented and then undone).  Each adjacency entry's claim-word read
+    stands in for the method's degree read, so it adds nothing."""
     extra_atomics = st["atomics"] - kcore_pkc_atomics(m, sum_core)
     return {"extra_atomics": int(extra_atomics), "bytes": int(n // 8 + 4 * st["rem_scanned"] + 8 * n
-                                                               + 4 * st["rem_written"] + 8 * extra_atomics
-                                                               - 4 * 2 * m)}
+                                                               + 4 * st["rem_written"] + 8 * extra_atomics)}
 
 
 KERNEL_SOURCES = {
@@ -347,6 +353,40 @@ def run_cbds_timing(args, g, core_d, set_d, flush, stream, n, m):
             "roofline": roof, "k_star": r.k_star, "E_core": r.E_core, "V_core": r.V_core, "E": r.E, "V": r.V,
             "n_legit": r.n_legit,
             "note": "dsg_cbds with the step's core numbers supplied on the device (densest core + second phase)"}
+
+
+def run_lazy_compare(args, wl, dsg, n, src_d, dst_d, flush, stream, m, peel_stats):
+    """The peel of the step's first eps with thin-tail lazy rounds on and off
+    (same results, checked): launch time (CUDA events, L2 flushed before
+    each), rounds, lazy rounds, vertex tests of the threshold passes, and the
+    algorithmic bytes of each (the byte model's per-round alive id + state
+    reads count the vertices a round actually tests)."""
+    import torch
+    p, q = wl["eps"][0]
+    g = dsg.Graph.from_edges(n, src_d, dst_d, stream=stream)
+    res = {}
+    for mode in ("on", "off"):
+        dsg.set_tuning(peel_lazy=(mode == "on"))
+        tr = g.bahmani_trace(p, q)
+        ms = []
+        for _ in range(max(3, args.steps)):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.bahmani(p, q, want_set=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[mode] = {"ms": round(min(ms), 4), "rounds": int(tr.rounds), "lazy_rounds": int(tr.lazy_rounds),
+                     "tested": int(tr.tested), "E": int(tr.E), "V": int(tr.V)}
+    dsg.set_tuning()
+    g.close()
+    on, off = res["on"], res["off"]
+    res["same_result"] = (on["E"], on["V"], on["rounds"]) == (off["E"], off["V"], off["rounds"])
+    res["speedup"] = round(off["ms"] / on["ms"], 3) if on["ms"] else None
+    res["tests_saved"] = off["tested"] - on["tested"]
+    return res
 
 
 # ----------------------------------------------------------------- our arm
@@ -484,6 +524,8 @@ def run_ours(args, wl, raw, rank, world):
         "tuning": tuning,
     }
 
+    if wl.get("lazy_compare"):
+        out["peel_lazy"] = run_lazy_compare(args, wl, dsg, n, src_d, dst_d, flush, stream, m, peel_stats)
     if not args.no_cbds:
         g = dsg.Graph.from_edges(n, src_d, dst_d, stream=stream)
         g.kcore(out=core_d)
@@ -994,6 +1036,7 @@ def main():
             "kernel_ms_per_step": res["kernel_ms"],
             "peel_rounds": res["peel_rounds"],
             "kcore_counters": res["kcore"],
+            "peel_lazy": res.get("peel_lazy"),
             "results": res["results"],
             "cbds": res.get("cbds"),
         }

@@ -137,6 +137,8 @@ typedef struct {
     uint64_t edges_scanned; /* out: adjacency entries read by the neighbour scans (= 2m) */
     uint64_t decrements;    /* out: degree decrements of surviving neighbours (edges whose
                                ends failed in different rounds) */
+    uint64_t tested;        /* out: vertex tests of the threshold passes, summed over the rounds */
+    uint64_t lazy_rounds;   /* out: rounds that tested only the candidate list (see dsg_set_peel_lazy) */
 } dsg_trace;
 
 /* As dsg_bahmani, recording the per-round history.  DSG_EOVERFLOW if
@@ -407,6 +409,18 @@ dsg_status dsg_set_inline_max(uint32_t inline_max);
  * 0 turns it off; at most 131072 (16 blocks of 8192 vertices).  Default
  * 65536; DSG_KCORE_TAIL.  Results never depend on it. */
 dsg_status dsg_set_kcore_tail(uint32_t max_vertices);
+/* Peel (Algorithm 1) in a thin tail: once a round removes less than 1/8 of
+ * the vertices left, the next round also collects candidates -- every alive
+ * vertex whose degree is at or below a bound B = T + floor(T/128) (T the
+ * round's threshold), from the surviving vertices it tests and from the
+ * decrements that bring a degree down to B -- and a following round whose
+ * threshold is at most B and whose candidates number less than a quarter of
+ * the vertices left tests only those candidates instead of every alive
+ * vertex.  A vertex failing in that round has degree <= T <= B and so is
+ * among them: the rounds are the same, with fewer vertex tests
+ * (dsg_trace.tested).  1 (default) on, 0 off; DSG_PEEL_LAZY.  Results never
+ * depend on it. */
+dsg_status dsg_set_peel_lazy(uint32_t on);
 
 /*
  * Densest k-core and CBDS-P (Algorithm 2).

@@ -33,13 +33,14 @@ def round_bound(n: int, p: int, q: int) -> int:
 
 def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, chunk_len: int = 256,
                hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384, inline_max: int = 4096,
-               kcore_tail: int = 65536, batch_split: int = 0):
+               kcore_tail: int = 65536, batch_split: int = 0, peel_lazy: bool = True):
     N.check(lib().dsg_set_tuning(block, blocks_per_sm, short_max, chunk_len), "set_tuning")
     N.check(lib().dsg_set_hot_degree(hot_deg), "set_hot_degree")
     N.check(lib().dsg_set_local_max(local_max, local_work), "set_local_max")
     N.check(lib().dsg_set_inline_max(inline_max), "set_inline_max")
     N.check(lib().dsg_set_kcore_tail(kcore_tail), "set_kcore_tail")
     N.check(lib().dsg_set_batch_split(batch_split), "set_batch_split")
+    N.check(lib().dsg_set_peel_lazy(1 if peel_lazy else 0), "set_peel_lazy")
 
 
 def get_tuning():
@@ -110,6 +111,8 @@ class Trace:
     mask: object
     edges_scanned: int
     decrements: int
+    tested: int = 0
+    lazy_rounds: int = 0
 
 
 @dataclass
@@ -225,7 +228,7 @@ class Graph:
             peel_round = np.zeros(max(self.n, 1), np.uint32)
         if out_set is None:
             out_set = np.zeros(max(self.n, 1), np.uint8)
-        t = N.Trace(0, 0, 0, 0, hist_cap, N.ptr(hs), N.ptr(he), N.ptr(peel_round), N.ptr(out_set), 0, 0)
+        t = N.Trace(0, 0, 0, 0, hist_cap, N.ptr(hs), N.ptr(he), N.ptr(peel_round), N.ptr(out_set), 0, 0, 0, 0)
         N.check(lib().dsg_bahmani_trace(self._h, p, q, ctypes.byref(t)), "bahmani_trace")
         R = t.rounds
         if isinstance(peel_round, np.ndarray):
@@ -233,7 +236,7 @@ class Graph:
         if isinstance(out_set, np.ndarray):
             out_set = out_set[:self.n]
         return Trace(R, t.best_round, t.best_E, t.best_V, hs[:R + 1].copy(), he[:R + 1].copy(), peel_round,
-                     out_set, t.edges_scanned, t.decrements)
+                     out_set, t.edges_scanned, t.decrements, t.tested, t.lazy_rounds)
 
     def autotune(self, p: int = 1, q: int = 10, peel: bool = True, kcore: bool = True) -> int:
         """Pick launch parameters for this graph's size class (dsg_autotune);

@@ -36,7 +36,8 @@ class DsgError(RuntimeError):
 class Trace(c.Structure):
     _fields_ = [("rounds", c.c_uint64), ("best_round", c.c_uint64), ("best_E", c.c_uint64),
                 ("best_V", c.c_uint64), ("hist_cap", c.c_uint64), ("hist_S", _VP), ("hist_E", _VP),
-                ("peel_round", _VP), ("out_set", _VP), ("edges_scanned", c.c_uint64), ("decrements", c.c_uint64)]
+                ("peel_round", _VP), ("out_set", _VP), ("edges_scanned", c.c_uint64), ("decrements", c.c_uint64),
+                ("tested", c.c_uint64), ("lazy_rounds", c.c_uint64)]
 
 
 class Batch(c.Structure):
@@ -131,6 +132,7 @@ _SIGS = [
     ("dsg_set_inline_max", c.c_int, [c.c_uint32]),
     ("dsg_set_kcore_tail", c.c_int, [c.c_uint32]),
     ("dsg_set_batch_split", c.c_int, [c.c_uint32]),
+    ("dsg_set_peel_lazy", c.c_int, [c.c_uint32]),
     ("dsg_set_allocator", None, [ALLOC_FN, FREE_FN, _VP]),
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),
     ("dsg_debug_peel_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, _U64P, c.c_uint64, _U64P]),

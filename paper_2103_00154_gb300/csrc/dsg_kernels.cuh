@@ -32,6 +32,8 @@ struct Tuning {
     uint32_t batch_split = 0;    // batches: a graph whose work (2m + n) exceeds this is solved by the
                                  // grid-wide kernels (0: above twice a block's share and 2^20)
     uint32_t batch_block = 512;  // batches: threads per block of the block-per-graph kernel
+    uint32_t peel_lazy = 1;      // peel: thin-tail rounds test only the candidate list (0: every round
+                                 // tests the whole alive list); read from the global tuning only
 };
 
 // Tuning of a batch of G graphs with `work` = sum of (2m + n): the autotuned

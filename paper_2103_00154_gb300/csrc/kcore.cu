@@ -218,7 +218,7 @@ __device__ __forceinline__ uint64_t queue_row(const CoreArgs& a, CoreLevel* P, u
 }
 
 template <int TB>
-__global__ void __launch_bounds__(TB) kcore_kernel(CoreArgs a) {
+__global__ void __launch_bounds__(TB, TB == 256 ? 3 : 1) kcore_kernel(CoreArgs a) {
     __shared__ CoreSmem<TB> sm;
     CoreCtl* ctl = a.ctl;
     const uint32_t tid = threadIdx.x;

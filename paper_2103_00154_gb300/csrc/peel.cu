@@ -58,6 +58,9 @@ struct __align__(128) PeelCtl {
     unsigned long long pad6[15];
     unsigned long long dec;     // alive-neighbour decrements (D)
     unsigned long long pad7[15];
+    unsigned long long cand;    // cursor of candidate-list writes (all rounds)
+    unsigned long long pad8[15];
+    unsigned long long tested, lazy_rounds;  // statistics kept by block 0: vertex tests, lazy rounds
     unsigned long long rounds, best_round, best_E, best_V;
     unsigned long long stamps;
     unsigned long long cur_S, cur_E;  // |S_r| and |E(S_r)| where the launch stopped
@@ -77,6 +80,8 @@ struct PeelArgs {
     uint32_t* FL;         // ... and length of each F entry (else read from off)
     uint64_t* C;
     uint32_t* map;        // status map, (n + 15) / 16 words
+    uint32_t* candA;      // nullable (then no lazy rounds): two candidate lists of n entries
+    uint32_t* candB;
     uint64_t* hist_S;
     uint64_t* hist_E;
     uint64_t hist_cap;
@@ -132,6 +137,15 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
     uint64_t short_lo = 0, chunk_lo = 0, surv_base = 0;
     const uint32_t* alive = nullptr;  // first round: identity (a fresh peel) or every vertex (a resumed one)
     uint32_t* next = a.listA;
+    uint64_t alive_len = 0;           // entries of `alive` (after lazy rounds some of them have failed)
+    // lazy rounds (thin tail): the candidate list holds every alive vertex whose degree is at or below
+    // the bound B; a round whose threshold is within B tests only that list
+    const bool lazy_ok = a.candA != nullptr;
+    uint32_t* cur_cand = a.candA;
+    uint32_t* next_cand = a.candB;
+    uint64_t cand_n = 0, cand_base = 0, S_prev = S;
+    bool have_cands = false;
+    uint32_t B = 0;
     uint64_t best_E = resume ? a.best_E0 : E, best_V = resume ? a.best_V0 : S;
     uint64_t best_round = resume ? a.best_round0 : 0;
     uint64_t nstamp = 0;
@@ -157,7 +171,17 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         const bool fresh = r == 0;                  // identity list, degrees from the rows
         const bool scan_all = !alive && resume;     // a resumed peel's first round: every vertex, failed ones skipped
         const bool by_id = fresh || scan_all;
-        const uint64_t span = scan_all ? a.n : S;
+        // thin: the last round removed less than 1/8 of the vertices; then this round collects the
+        // next round's candidates (bound Bn), and it is lazy when the current list covers T
+        const bool thin = lazy_ok && !fresh && (S_prev - S) * 8 < S_prev;
+        const bool lazy = thin && have_cands && !by_id && T <= B && cand_n * 4 < S;
+        const uint32_t Bn = lazy ? B : (thin ? T + T / 128u : 0u);
+        const uint64_t span = by_id ? (scan_all ? a.n : S) : (lazy ? cand_n : alive_len);
+        const uint32_t* src = lazy ? cur_cand : alive;
+        if (blockIdx.x == 0 && tid == 0) {
+            ctl->tested += span;
+            ctl->lazy_rounds += lazy ? 1u : 0u;
+        }
         // a tile is `items` slices of TB: thread tid takes i = t + j TB + tid for
         // j < items (4 in the by-id rounds, whose tiles would otherwise be
         // short; 1 on the alive list); the first pass tests and marks, the
@@ -165,7 +189,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         const uint32_t items = by_id ? 4u : 1u;
         uint64_t X = 0;
         for (uint64_t t = (uint64_t)blockIdx.x * TB * items; t < span; t += (uint64_t)gridDim.x * TB * items) {
-            uint32_t fail_m = 0, short_m = 0, surv_m = 0, nch_sum = 0;
+            uint32_t fail_m = 0, short_m = 0, surv_m = 0, cand_m = 0, nch_sum = 0;
             uint64_t c_beg = 0, c_len = 0;  // the alive-list rounds' one item: its row, for the second pass
             for (uint32_t j = 0; j < items; ++j) {
                 const uint64_t i = t + (uint64_t)j * TB + tid;
@@ -185,8 +209,9 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                             gone = (d & kDead) != 0;
                         }
                     } else {
-                        v = alive[i];
+                        v = src[i];
                         d = a.st[v];
+                        gone = (d & kDead) != 0;  // an alive list left from before lazy rounds
                     }
                 }
                 const bool hub = by_id && valid && len >= hot;
@@ -208,7 +233,8 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                         fail_m |= 1u << j;
                         if (!by_id) atomicOr(&a.map[v >> 4], 1u << (2u * (v & 15u)));
                     } else {
-                        surv_m |= 1u << j;
+                        if (!lazy) surv_m |= 1u << j;
+                        if (thin && d <= Bn) cand_m |= 1u << j;
                         if (fresh) a.st[v] = d;
                     }
                 }
@@ -269,7 +295,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
             for (uint32_t j = 0; j < items; ++j) {
                 const uint64_t i = t + (uint64_t)j * TB + tid;
                 uint32_t v = 0, nch = 0;
-                if ((fail_m | surv_m) >> j & 1u) v = by_id ? (uint32_t)i : alive[i];
+                if ((fail_m | surv_m | cand_m) >> j & 1u) v = by_id ? (uint32_t)i : src[i];
                 if (short_m >> j & 1u) {
                     a.F[at_s] = v;
                     if (a.FB) {
@@ -285,6 +311,14 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                 {
                     const uint32_t sb = __ballot_sync(kFullMask, surv_m >> j & 1u);
                     if (surv_m >> j & 1u) next[v0 + sm.surv_at[j][tid >> 5] + __popc(sb & lanemask_lt())] = v;
+                    // candidates for the next round: one atomic per warp
+                    const uint32_t cb = __ballot_sync(kFullMask, cand_m >> j & 1u);
+                    if (cb) {
+                        unsigned long long cbase = 0;
+                        if (lane == 0) cbase = atomicAdd(&ctl->cand, (unsigned long long)__popc(cb));
+                        cbase = __shfl_sync(kFullMask, cbase, 0);
+                        if (cand_m >> j & 1u) next_cand[cbase - cand_base + __popc(cb & lanemask_lt())] = v;
+                    }
                 }
                 // chunk items of the warp's long failures, written by the whole warp
                 // (a hub has hundreds of them)
@@ -326,8 +360,15 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
                 if (!(valid >> j & 1u)) continue;
                 const uint32_t b = w[j] >> (2u * (u[j] & 15u));
                 if (!(b & 1u)) {
-                    // alive: one degree less (hubs' decrements combined in the block)
-                    if (!(b & 2u) || !agg_add(sm.agg, u[j])) atomicSub(&st[u[j]], 1u);
+                    // alive: one degree less (hubs' decrements combined in the block); in a thin
+                    // round the decrement that takes a degree to the bound makes it a candidate
+                    if ((b & 2u) && agg_add(sm.agg, u[j])) {
+                    } else if (thin) {
+                        const uint32_t old = atomicSub(&st[u[j]], 1u);
+                        if (old > Bn && old - 1u <= Bn) next_cand[atomicAdd(&ctl->cand, 1ull) - cand_base] = u[j];
+                    } else {
+                        atomicSub(&st[u[j]], 1u);
+                    }
                     ++ndec;
                 }
             }
@@ -339,7 +380,13 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
         for (uint32_t i = tid; i < kAggSlots; i += TB) {
             uint32_t key = sm.agg.key[i];
             if (key != kAggEmpty) {
-                atomicSub(&st[key], sm.agg.cnt[i]);
+                const uint32_t c = sm.agg.cnt[i];
+                if (thin) {
+                    const uint32_t old = atomicSub(&st[key], c);
+                    if (old > Bn && old - c <= Bn) next_cand[atomicAdd(&ctl->cand, 1ull) - cand_base] = key;
+                } else {
+                    atomicSub(&st[key], c);
+                }
                 sm.agg.key[i] = kAggEmpty;
                 sm.agg.cnt[i] = 0;
             }
@@ -366,11 +413,27 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
             best_E = E1;
             best_V = S1;
         }
-        surv_base += S1;
         short_lo = short_hi;
         chunk_lo = chunk_hi;
-        alive = next;
-        next = (next == a.listA) ? a.listB : a.listA;
+        if (!lazy) {  // a lazy round leaves the alive list as it was (its failures are skipped later)
+            surv_base += S1;
+            alive_len = S1;
+            alive = next;
+            next = (next == a.listA) ? a.listB : a.listA;
+        }
+        {
+            const uint64_t cand_hi = ld_relaxed_u64(&ctl->cand);
+            if (thin) {
+                uint32_t* t_ = cur_cand;
+                cur_cand = next_cand;
+                next_cand = t_;
+                cand_n = cand_hi - cand_base;
+                B = Bn;
+            }
+            have_cands = thin;
+            cand_base = cand_hi;
+        }
+        S_prev = S;
         S = S1;
         E = E1;
         if (r >= a.hist_cap) break;
@@ -480,6 +543,11 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
     DSG_TRY_CUDA(sc.get(&a.FL, n));
     DSG_TRY_CUDA(sc.get(&a.C, chunk_cap));
     DSG_TRY_CUDA(sc.get(&a.map, ((size_t)n + 15) / 16));
+    a.candA = a.candB = nullptr;
+    if (current_tuning().peel_lazy) {
+        DSG_TRY_CUDA(sc.get(&a.candA, n));
+        DSG_TRY_CUDA(sc.get(&a.candB, n));
+    }
     DSG_TRY_CUDA(sc.get(&a.hist_S, cap));
     DSG_TRY_CUDA(sc.get(&a.hist_E, cap));
     DSG_TRY_CUDA(sc.get(&a.ctl, 1));
@@ -661,6 +729,8 @@ dsg_status dsg_bahmani_trace(const dsg_graph* g, uint32_t eps_num, uint32_t eps_
     t->best_V = g->n ? c.best_V : 0;
     t->edges_scanned = 2 * g->m;
     t->decrements = g->n ? c.dec : 0;
+    t->tested = g->n ? c.tested : 0;
+    t->lazy_rounds = g->n ? c.lazy_rounds : 0;
     if (t->hist_cap < c.rounds + 1 && (t->hist_S || t->hist_E)) {
         set_error("bahmani_trace: history needs %llu slots, got %llu", (unsigned long long)(c.rounds + 1),
                   (unsigned long long)t->hist_cap);
@@ -841,6 +911,8 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     a.FL = nullptr;
     a.C = reinterpret_cast<uint64_t*>(base + o); o += b_chunk;
     a.map = reinterpret_cast<uint32_t*>(base + o); o += b_map;
+    a.candA = nullptr;  // no lazy rounds: every round tests the whole alive list
+    a.candB = nullptr;
     a.hist_S = reinterpret_cast<uint64_t*>(base + o); o += b_hist;
     a.hist_E = reinterpret_cast<uint64_t*>(base + o); o += b_hist;
     a.ctl = reinterpret_cast<PeelCtl*>(base + o);
@@ -896,7 +968,8 @@ struct dsg_peel_state {
     uint64_t r = 0, S = 0, E = 0, best_round = 0, best_E = 0, best_V = 0, cap = 0, chunk_cap = 0;
     bool done = false;
     dsg::Tuning tu;
-    uint32_t *st = nullptr, *listA = nullptr, *listB = nullptr, *F = nullptr, *FL = nullptr, *map = nullptr;
+    uint32_t *st = nullptr, *listA = nullptr, *listB = nullptr, *F = nullptr, *FL = nullptr, *map = nullptr,
+             *candA = nullptr, *candB = nullptr;
     uint64_t *FB = nullptr, *C = nullptr, *hist_S = nullptr, *hist_E = nullptr;
     dsg::PeelCtl* ctl = nullptr;
 };
@@ -909,8 +982,8 @@ static constexpr uint64_t kSnapHeaderWords = 16;
 static void peel_state_release(dsg_peel_state* ps) {
     if (!ps) return;
     cudaStream_t s = ps->g ? ps->g->stream : nullptr;
-    void* bufs[] = {ps->st, ps->listA, ps->listB, ps->F, ps->FB, ps->FL, ps->C, ps->map, ps->hist_S, ps->hist_E,
-                    ps->ctl};
+    void* bufs[] = {ps->st,  ps->listA,  ps->listB,  ps->F,      ps->FB,     ps->FL, ps->C,
+                    ps->map, ps->candA,  ps->candB,  ps->hist_S, ps->hist_E, ps->ctl};
     for (void* b : bufs)
         if (b) dev_free(b, s);
     if (s) cudaStreamSynchronize(s);
@@ -941,6 +1014,8 @@ static dsg_status peel_state_new(const dsg_graph* g, uint32_t p, uint32_t q, dsg
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->F, nb, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->FB, 2 * nb, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->FL, nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->candA, nb, s);
+    if (e == cudaSuccess) e = dev_alloc((void**)&ps->candB, nb, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->C, ps->chunk_cap * 8, s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->map, (((size_t)(n ? n : 1) + 15) / 16 * 4 + 255) & ~size_t(255), s);
     if (e == cudaSuccess) e = dev_alloc((void**)&ps->hist_S, ps->cap * 8, s);
@@ -975,6 +1050,9 @@ static dsg_status peel_state_run(dsg_peel_state* ps, uint64_t max_rounds) {
     a.FL = ps->FL;
     a.C = ps->C;
     a.map = ps->map;
+    const bool lazy_on = current_tuning().peel_lazy != 0;
+    a.candA = lazy_on ? ps->candA : nullptr;
+    a.candB = lazy_on ? ps->candB : nullptr;
     a.hist_S = ps->hist_S;
     a.hist_E = ps->hist_E;
     a.hist_cap = ps->cap;

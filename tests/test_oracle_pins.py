@@ -444,3 +444,25 @@ def test_table3_cbds_not_below_the_eps0_peel_on_synthetic_graphs():
         me, mv, _, _ = oracle.cbds_phase2(c, core, k, Ek, Vk)
         assert Fraction(me, mv) >= Fraction(peel0.E, peel0.V), raw.name
         assert Fraction(me, mv) >= Fraction(Ek, Vk), raw.name  # phase 2 never loses density (Sec. 3.2)
+
+
+def test_onion_shells_peel_one_per_round():
+    # the nested-shell generator: every vertex of shell i >= 1 has exactly d edges into
+    # shell i - 1 and every vertex inside gets at least d + 1 from its outer shell, so at
+    # eps < 1/(2d) each round of the peel removes the outermost shell and nothing else
+    raw = inputs.onion(1 << 12, 8, 24)
+    c = oracle.from_raw(raw)
+    deg = np.diff(c.off.astype(np.int64))
+    sizes = [24]
+    while sum(sizes) < 1 << 12:
+        sizes.append(-(-sizes[-1] * 9 // 8))
+    assert raw.n == sum(sizes)
+    outer = deg[raw.n - sizes[-1]:]
+    assert (outer == 8).all()
+    inner = deg[24:raw.n - sizes[-1]]
+    assert inner.min() >= 2 * 8 + 1
+    r = oracle.bahmani(c, 1, 1000)
+    assert r.rounds >= len(sizes) - 3
+    # round t removes exactly the outermost remaining shell
+    for t in range(1, 10):
+        assert int(r.hist_S[t - 1] - r.hist_S[t]) == sizes[-t]
