@@ -322,8 +322,13 @@ typedef struct {
     uint64_t big_work;     /* a request whose 2 m_raw + n exceeds this is solved on its own by the
                               grid-wide kernels on big_sms SMs, not in a block-per-graph batch
                               (0: 2^23; UINT64_MAX: never) */
-    uint32_t big_sms;      /* SMs the grid-wide solves of big requests use (0: a quarter of them);
-                              the block-per-graph batches use the rest */
+    uint32_t big_sms;      /* SMs each grid-wide solve of a big request uses (0: a quarter of them
+                              divided by big_threads); the block-per-graph batches use the rest */
+    uint64_t max_batch_work; /* a launch closes before the next ready request would take its summed
+                                work (2m + n of its graphs) past this, so one launch's run time, and
+                                the wait of the requests behind it, stays bounded (0: no limit) */
+    uint32_t big_threads;  /* host threads solving big requests, each on its own stream with big_sms
+                              SMs (0: 1) */
 } dsg_serve_config;
 
 #define DSG_REQ_BORROW 0x1u   /* src/dst stay valid and unchanged until the request completes: no copy */
@@ -354,6 +359,12 @@ typedef struct {
     double p50_us, p99_us;   /* latency of completed requests */
     double graphs_per_s;     /* completed / uptime */
     double uptime_s;
+    /* where the time went: requests solved alone by the grid-wide kernels,
+     * host seconds the ingest threads spent ingesting (summed over threads)
+     * and the big-request thread spent solving, and device seconds of the
+     * block-per-graph launches (summed over launches, which may overlap) */
+    uint64_t big_done;
+    double ingest_busy_s, big_busy_s, batch_device_s;
 } dsg_serve_info;
 
 dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out);
@@ -421,6 +432,13 @@ dsg_status dsg_set_kcore_tail(uint32_t max_vertices);
  * (dsg_trace.tested).  1 (default) on, 0 off; DSG_PEEL_LAZY.  Results never
  * depend on it. */
 dsg_status dsg_set_peel_lazy(uint32_t on);
+/* Peel (Algorithm 1): 1 reads the long rows' chunks as aligned 16-byte
+ * groups, four consecutive entries per lane (one 128-bit load each, entries
+ * outside the chunk masked off); 0 (default) reads one entry per lane, 32
+ * consecutive entries per warp load, four loads in flight.  Used only when
+ * the adjacency array is 16-byte aligned.  DSG_PEEL_VEC.  Results never
+ * depend on it. */
+dsg_status dsg_set_peel_vec(uint32_t on);
 
 /*
  * Densest k-core and CBDS-P (Algorithm 2).

@@ -33,7 +33,7 @@ def round_bound(n: int, p: int, q: int) -> int:
 
 def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, chunk_len: int = 256,
                hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384, inline_max: int = 4096,
-               kcore_tail: int = 65536, batch_split: int = 0, peel_lazy: bool = True):
+               kcore_tail: int = 65536, batch_split: int = 0, peel_lazy: bool = True, peel_vec: bool = False):
     N.check(lib().dsg_set_tuning(block, blocks_per_sm, short_max, chunk_len), "set_tuning")
     N.check(lib().dsg_set_hot_degree(hot_deg), "set_hot_degree")
     N.check(lib().dsg_set_local_max(local_max, local_work), "set_local_max")
@@ -41,6 +41,7 @@ def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, ch
     N.check(lib().dsg_set_kcore_tail(kcore_tail), "set_kcore_tail")
     N.check(lib().dsg_set_batch_split(batch_split), "set_batch_split")
     N.check(lib().dsg_set_peel_lazy(1 if peel_lazy else 0), "set_peel_lazy")
+    N.check(lib().dsg_set_peel_vec(1 if peel_vec else 0), "set_peel_vec")
 
 
 def get_tuning():
@@ -473,8 +474,10 @@ class Server:
     poll() returns a dict of the request's results or None while pending."""
 
     def __init__(self, max_batch: int = 0, max_pending: int = 0, hbm_budget: int = 0, max_inflight: int = 0,
-                 ingest_threads: int = 0, big_work: int = 0, big_sms: int = 0):
-        cfg = N.ServeConfig(max_batch, max_pending, hbm_budget, max_inflight, ingest_threads, big_work, big_sms)
+                 ingest_threads: int = 0, big_work: int = 0, big_sms: int = 0, max_batch_work: int = 0,
+                 big_threads: int = 0):
+        cfg = N.ServeConfig(max_batch, max_pending, hbm_budget, max_inflight, ingest_threads, big_work, big_sms,
+                            max_batch_work, big_threads)
         h = ctypes.c_void_p()
         N.check(lib().dsg_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "serve_create")
         self._h = h

@@ -53,7 +53,7 @@ class BatchResult(c.Structure):
 class ServeConfig(c.Structure):
     _fields_ = [("max_batch", c.c_uint32), ("max_pending", c.c_uint32), ("hbm_budget", c.c_uint64),
                 ("max_inflight", c.c_uint32), ("ingest_threads", c.c_uint32), ("big_work", c.c_uint64),
-                ("big_sms", c.c_uint32)]
+                ("big_sms", c.c_uint32), ("max_batch_work", c.c_uint64), ("big_threads", c.c_uint32)]
 
 
 class Request(c.Structure):
@@ -72,7 +72,8 @@ class ServeStats(c.Structure):
                 ("rejected", c.c_uint64), ("pending", c.c_uint64), ("in_flight", c.c_uint64),
                 ("batches", c.c_uint64), ("hbm_in_use", c.c_uint64), ("hbm_budget", c.c_uint64),
                 ("p50_us", c.c_double), ("p99_us", c.c_double), ("graphs_per_s", c.c_double),
-                ("uptime_s", c.c_double)]
+                ("uptime_s", c.c_double), ("big_done", c.c_uint64), ("ingest_busy_s", c.c_double),
+                ("big_busy_s", c.c_double), ("batch_device_s", c.c_double)]
 
 
 class CbdsResult(c.Structure):
@@ -133,6 +134,7 @@ _SIGS = [
     ("dsg_set_kcore_tail", c.c_int, [c.c_uint32]),
     ("dsg_set_batch_split", c.c_int, [c.c_uint32]),
     ("dsg_set_peel_lazy", c.c_int, [c.c_uint32]),
+    ("dsg_set_peel_vec", c.c_int, [c.c_uint32]),
     ("dsg_set_allocator", None, [ALLOC_FN, FREE_FN, _VP]),
     ("dsg_debug_wait_timeout", c.c_int, [c.c_uint32, c.c_uint64]),
     ("dsg_debug_peel_trace", c.c_int, [_VP, c.c_uint32, c.c_uint32, _U64P, c.c_uint64, _U64P]),

@@ -34,6 +34,8 @@ struct Tuning {
     uint32_t batch_block = 512;  // batches: threads per block of the block-per-graph kernel
     uint32_t peel_lazy = 1;      // peel: thin-tail rounds test only the candidate list (0: every round
                                  // tests the whole alive list); read from the global tuning only
+    uint32_t peel_vec = 0;       // peel: long rows read as aligned 128-bit groups (0: one entry per lane);
+                                 // read from the global tuning only
 };
 
 // Tuning of a batch of G graphs with `work` = sum of (2m + n): the autotuned
@@ -430,12 +432,15 @@ __device__ __forceinline__ void walk_all_entries(const uint64_t* __restrict__ of
 // this block's warps walk it; C is ignored.
 // FB / FL (nullable): row starts and lengths stored beside F, saving the
 // offset loads of the short rows.
+// vec_end (0: off): adj is 16-byte aligned and holds at least vec_end
+// entries; long rows are then read with 128-bit loads.
 template <int TB, bool LOCAL = false, class Fn>
 __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
                                               const uint32_t* F, uint64_t lo, uint64_t hi,
                                               const uint64_t* __restrict__ C, uint64_t clo, uint64_t chi,
                                               uint32_t chunk_len, Fn& fn, uint32_t dbg_n = 0,
-                                              const uint64_t* FB = nullptr, const uint32_t* FL = nullptr) {
+                                              const uint64_t* FB = nullptr, const uint32_t* FL = nullptr,
+                                              uint64_t vec_end = 0) {
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31u;
     const uint64_t gw = LOCAL ? (uint64_t)(tid >> 5) : ((uint64_t)blockIdx.x * TB + tid) >> 5;
@@ -509,6 +514,36 @@ __device__ __forceinline__ void scan_frontier(const uint64_t* __restrict__ off, 
         uint64_t b = off[v], e_end = off[v + 1];
         uint64_t beg = b + c * chunk_len;
         uint64_t end = min(e_end, beg + chunk_len);
+        if (vec_end) {
+            // 128-bit loads: lane l takes the aligned group of four entries 4g..4g+3, g = g0 + l
+            // (+ 32 per step); entries of a group outside [beg, end) are masked off, and a
+            // group that reaches past vec_end is read entry by entry
+            static_assert(kBatch == 4, "one 16-byte group per visitor call");
+            const uint64_t g0 = beg >> 2, g1 = (end + 3) >> 2;
+            for (uint64_t gb = g0; gb < g1; gb += 32) {
+                const uint64_t g = gb + lane;
+                uint32_t bu[kBatch] = {0u, 0u, 0u, 0u}, bv[kBatch] = {v, v, v, v}, valid = 0;
+                if (g < g1) {
+                    const uint64_t e0 = g * 4;
+                    if (e0 + 4 <= vec_end) {
+                        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(adj) + g);
+                        bu[0] = q.x;
+                        bu[1] = q.y;
+                        bu[2] = q.z;
+                        bu[3] = q.w;
+                    } else {
+#pragma unroll
+                        for (uint32_t j = 0; j < kBatch; ++j)
+                            if (e0 + j >= beg && e0 + j < end) bu[j] = ld_stream(adj + e0 + j);
+                    }
+#pragma unroll
+                    for (uint32_t j = 0; j < kBatch; ++j)
+                        if (e0 + j >= beg && e0 + j < end) valid |= 1u << j;
+                }
+                fn(bu, bv, valid);
+            }
+            return;
+        }
         for (uint64_t j0 = beg + lane; j0 < end; j0 += 32 * kBatch) {
             uint32_t bu[kBatch], bv[kBatch], valid = 0;
 #pragma unroll

@@ -90,6 +90,7 @@ struct PeelArgs {
     uint32_t short_max;
     uint32_t chunk_len;
     uint32_t hot_deg;
+    uint32_t vec_loads;   // 1: long rows read as aligned 128-bit groups when adj is 16-byte aligned
     uint64_t* trace;      // nullable: block 0 stamps %globaltimer after every barrier
     uint64_t trace_cap;
     // resuming a paused peel (r0 > 0): the state words in st are the pause's,
@@ -156,6 +157,9 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
     stamp();
     agg_clear(sm.agg);
     const uint32_t hot = hot_threshold(a.hot_deg);
+    // long rows by 128-bit loads when the adjacency is 16-byte aligned (a view into a packed
+    // batch may not be); groups are only read whole inside the 2m entries
+    const uint64_t vec_end = (a.vec_loads && (reinterpret_cast<uintptr_t>(a.adj) & 15u) == 0) ? 2 * a.m : 0;
     if (blockIdx.x == 0 && tid == 0 && !resume) {
         a.hist_S[0] = S;
         a.hist_E[0] = E;
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(TB, 65536 / (TB * 40)) peel_kernel(PeelArgs a)
             }
         };
         scan_frontier<TB>(a.off, a.adj, a.F, short_lo, short_hi, a.C, chunk_lo, chunk_hi, a.chunk_len, visit, a.n,
-                          a.FB, a.FL);
+                          a.FB, a.FL, vec_end);
         // flush the combined hub decrements (block_sum below synchronises first)
         __syncthreads();
         for (uint32_t i = tid; i < kAggSlots; i += TB) {
@@ -532,6 +536,7 @@ static dsg_status run_peel(const dsg_graph* g, uint32_t p, uint32_t q, uint64_t*
     a.short_max = tu.short_max;
     a.chunk_len = tu.chunk_len;
     a.hot_deg = tu.hot_deg;
+    a.vec_loads = current_tuning().peel_vec;
     a.trace = trace_dev;
     a.trace_cap = trace_cap;
     a.r0 = a.S0 = a.E0 = a.best_round0 = a.best_E0 = a.best_V0 = a.max_rounds = 0;
@@ -921,6 +926,7 @@ extern "C" dsg_status dsg_bahmani_noalloc(uint32_t n, const uint64_t* off, const
     a.short_max = tu.short_max;
     a.chunk_len = tu.chunk_len;
     a.hot_deg = tu.hot_deg;
+    a.vec_loads = current_tuning().peel_vec;
     a.trace = nullptr;
     a.trace_cap = 0;
     a.r0 = a.S0 = a.E0 = a.best_round0 = a.best_E0 = a.best_V0 = a.max_rounds = 0;
@@ -1061,6 +1067,7 @@ static dsg_status peel_state_run(dsg_peel_state* ps, uint64_t max_rounds) {
     a.short_max = ps->tu.short_max;
     a.chunk_len = ps->tu.chunk_len;
     a.hot_deg = ps->tu.hot_deg;
+    a.vec_loads = current_tuning().peel_vec;
     a.trace = nullptr;
     a.trace_cap = 0;
     a.r0 = ps->r;

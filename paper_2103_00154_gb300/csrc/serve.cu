@@ -14,9 +14,10 @@
 //   ingest  (ingest_threads host threads, each with its own stream) turn
 //           admitted requests into resident graphs; a request above
 //           big_work goes to the big-request thread, the rest to the batches;
-//   big     (one host thread) solves big requests one at a time with the
-//           grid-wide kernels on big_sms SMs (the batches get the others), so
-//           one large graph never holds a batch of small ones back;
+//   big     (big_threads host threads, each with its own stream) solve big
+//           requests one at a time each with the grid-wide kernels on big_sms
+//           SMs (the batches get the others), so one large graph never holds
+//           a batch of small ones back;
 //   poll    waits (bounded) for one ticket's completion.
 // A request's results do not depend on what it is batched with: each graph is
 // solved by its own block with its own state.
@@ -82,11 +83,12 @@ struct dsg_server {
     std::deque<dsg::ServeReq*> to_ingest, big;
     std::vector<std::thread> ingesters;
     std::vector<cudaStream_t> s_ingest;
-    std::thread big_worker;
-    cudaStream_t s_big = nullptr;
+    std::vector<std::thread> big_workers;
+    std::vector<cudaStream_t> s_big;
     bool stop_helpers = false;
     // statistics
-    uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, batches = 0;
+    uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, batches = 0, big_done = 0;
+    double ingest_busy_us = 0, big_busy_us = 0, batch_dev_ms = 0;
     std::vector<double> lat_us;
     double t0 = 0;
 };
@@ -108,7 +110,7 @@ struct Inflight {
     size_t tables_bytes = 0;
     std::vector<uint64_t> slot;
     uint64_t N = 0;
-    cudaEvent_t done_ev = nullptr;
+    cudaEvent_t start_ev = nullptr, done_ev = nullptr;
 };
 
 static void finish_request(dsg_server* s, ServeReq* r, dsg_status st) {
@@ -138,6 +140,7 @@ static bool is_big(const dsg_server* s, const ServeReq* r) {
 // Ingest one admitted request on stream st (synchronous for that stream only)
 // and hand it to the batches or to the big-request thread.
 static void ingest_one(dsg_server* s, ServeReq* r, cudaStream_t st_ing) {
+    const double t_in = now_us();
     dsg_graph* g = nullptr;
     dsg_status st = dsg_graph_from_edges(r->n, r->m_raw, r->src, r->dst, 0, st_ing, &g);
     if (r->owned) {
@@ -154,6 +157,7 @@ static void ingest_one(dsg_server* s, ServeReq* r, cudaStream_t st_ing) {
     const bool big = is_big(s, r);
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        s->ingest_busy_us += now_us() - t_in;
         if (big) s->big.push_back(r);
         else s->ready.push_back(r);
     }
@@ -178,29 +182,35 @@ static void ingest_main(dsg_server* s, cudaStream_t st) {
 
 // A big request alone: the peel (and core numbers) by the grid-wide kernels,
 // capped at big_sms blocks of one per SM, on the big stream.
-static void solve_big(dsg_server* s, ServeReq* r) {
+static void solve_big(dsg_server* s, ServeReq* r, cudaStream_t sb) {
+    const double t_in = now_us();
     dsg_graph view = *r->g;
     view.owns = false;
-    view.stream = s->s_big;
+    view.stream = sb;
     view.max_blocks = s->cfg.big_sms;
     view.force_block = 1024;
     dsg_status st = DSG_OK;
     uint8_t* set_dev = nullptr;
     if (r->out_set && r->n) {
-        if (dev_alloc((void**)&set_dev, r->n, s->s_big) != cudaSuccess) st = DSG_ENOMEM;
+        if (dev_alloc((void**)&set_dev, r->n, sb) != cudaSuccess) st = DSG_ENOMEM;
     }
     if (st == DSG_OK) st = peel_into(&view, r->p, r->q, set_dev, r->res);
     if (st == DSG_OK && r->out_set && r->n &&
-        (cudaMemcpyAsync(r->out_set, set_dev, r->n, cudaMemcpyDeviceToHost, s->s_big) != cudaSuccess ||
-         cudaStreamSynchronize(s->s_big) != cudaSuccess))
+        (cudaMemcpyAsync(r->out_set, set_dev, r->n, cudaMemcpyDeviceToHost, sb) != cudaSuccess ||
+         cudaStreamSynchronize(sb) != cudaSuccess))
         st = DSG_ECUDA;
-    if (set_dev) dev_free(set_dev, s->s_big);
+    if (set_dev) dev_free(set_dev, sb);
     if (st == DSG_OK && r->want_core && r->core && r->n) st = run_kcore(&view, r->core, nullptr, 0);
-    cudaStreamSynchronize(s->s_big);
+    cudaStreamSynchronize(sb);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->big_busy_us += now_us() - t_in;
+        s->big_done++;
+    }
     finish_request(s, r, st);
 }
 
-static void big_main(dsg_server* s) {
+static void big_main(dsg_server* s, cudaStream_t sb) {
     cudaSetDevice(s->device);
     for (;;) {
         ServeReq* r = nullptr;
@@ -211,7 +221,7 @@ static void big_main(dsg_server* s) {
             r = s->big.front();
             s->big.pop_front();
         }
-        solve_big(s, r);
+        solve_big(s, r, sb);
         s->cv_work.notify_one();
     }
 }
@@ -264,6 +274,8 @@ static dsg_status launch_batch(dsg_server* s, Inflight& f, cudaStream_t ss) {
     put(o_order, order.data(), G * 4);
     DSG_TRY_CUDA(cudaMemcpyAsync(base, host.data(), o_st, cudaMemcpyHostToDevice, ss));
     DSG_TRY_CUDA(cudaMemsetAsync(base + o_next, 0, 8, ss));
+    DSG_TRY_CUDA(cudaEventCreate(&f.start_ev));
+    DSG_TRY_CUDA(cudaEventRecord(f.start_ev, ss));
     BatchArgs& a = f.a;
     a.G = G;
     a.goff = reinterpret_cast<const uint64_t* const*>(base + o_goff);
@@ -285,12 +297,13 @@ static dsg_status launch_batch(dsg_server* s, Inflight& f, cudaStream_t ss) {
     a.hot_deg = 0;
     a.stats = nullptr;
     f.d_res = a.res;
-    // the batches leave the big-request thread's share of the SMs free
+    // the batches leave the big-request threads' share of the SMs free
     const uint32_t sms = (uint32_t)dev_info().sms;
-    const uint32_t big_sms = s->cfg.big_work == UINT64_MAX ? 0 : std::min(s->cfg.big_sms, sms - 1);
+    const uint32_t big_sms =
+        s->cfg.big_work == UINT64_MAX ? 0 : (uint32_t)std::min<uint64_t>((uint64_t)s->cfg.big_sms * s->cfg.big_threads, sms - 1);
     const uint32_t cap = (uint32_t)((uint64_t)batch_slots_for(512) * (sms - big_sms) / sms);
     DSG_TRY_CUDA(batch_launch(a, ss, 512, cap ? cap : 1));
-    DSG_TRY_CUDA(cudaEventCreateWithFlags(&f.done_ev, cudaEventDisableTiming));
+    DSG_TRY_CUDA(cudaEventCreate(&f.done_ev));
     DSG_TRY_CUDA(cudaEventRecord(f.done_ev, ss));
     // (the pageable staging vector may go: a host-to-device copy from pageable
     // memory has consumed its source when cudaMemcpyAsync returns)
@@ -320,11 +333,15 @@ static void complete_batch(dsg_server* s, Inflight& f, cudaStream_t ss) {
         for (int k = 0; k < 4; ++k) r->res[k] = res[4 * (size_t)i + k];
         finish_request(s, r, st);
     }
+    float dev_ms = 0;
+    if (cudaEventElapsedTime(&dev_ms, f.start_ev, f.done_ev) != cudaSuccess) dev_ms = 0;
     dev_free(f.d_tables, ss);
+    cudaEventDestroy(f.start_ev);
     cudaEventDestroy(f.done_ev);
     f = Inflight();
     std::lock_guard<std::mutex> lk(s->mu);
     s->batches++;
+    s->batch_dev_ms += dev_ms;
 }
 
 static void worker_main(dsg_server* s) {
@@ -372,7 +389,16 @@ static void worker_main(dsg_server* s) {
             std::vector<ServeReq*> batch;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
-                size_t take = std::min<size_t>(s->ready.size(), s->cfg.max_batch);
+                // in arrival order, at most max_batch graphs and max_batch_work of work (at least one)
+                size_t take = 0;
+                uint64_t work = 0;
+                while (take < s->ready.size() && take < s->cfg.max_batch) {
+                    const ServeReq* r = s->ready[take];
+                    const uint64_t w = 2 * r->m + r->n;
+                    if (take > 0 && work + w > s->cfg.max_batch_work) break;
+                    work += w;
+                    ++take;
+                }
                 batch.assign(s->ready.begin(), s->ready.begin() + take);
                 s->ready.erase(s->ready.begin(), s->ready.begin() + take);
             }
@@ -382,6 +408,8 @@ static void worker_main(dsg_server* s) {
             if (st != DSG_OK) {
                 for (ServeReq* r : fl[k].reqs) finish_request(s, r, st);
                 if (fl[k].d_tables) dev_free(fl[k].d_tables, s->s_solve[k]);
+                if (fl[k].start_ev) cudaEventDestroy(fl[k].start_ev);
+                if (fl[k].done_ev) cudaEventDestroy(fl[k].done_ev);
                 fl[k] = Inflight();
             } else {
                 running[k] = true;
@@ -410,32 +438,43 @@ dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out) {
     if (cfg) s->cfg = *cfg;
     else memset(&s->cfg, 0, sizeof(s->cfg));
     if (!s->cfg.max_batch) s->cfg.max_batch = 1024;
+    if (!s->cfg.max_batch_work) s->cfg.max_batch_work = UINT64_MAX;
     if (!s->cfg.max_pending) s->cfg.max_pending = 1u << 16;
     if (!s->cfg.max_inflight) s->cfg.max_inflight = 4;
     if (!s->cfg.ingest_threads) s->cfg.ingest_threads = 4;
     if (!s->cfg.big_work) s->cfg.big_work = 1ull << 23;
+    if (!s->cfg.big_threads) s->cfg.big_threads = 1;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess && !s->cfg.hbm_budget) {
         size_t fr = 0, tot = 0;
         e = cudaMemGetInfo(&fr, &tot);
         s->cfg.hbm_budget = fr / 2;
     }
-    if (e == cudaSuccess && !s->cfg.big_sms) s->cfg.big_sms = std::max(1, dev_info().sms / 4);
+    if (e == cudaSuccess && !s->cfg.big_sms)
+        s->cfg.big_sms = std::max<uint32_t>(1, (uint32_t)dev_info().sms / (4 * s->cfg.big_threads));
     s->s_ingest.assign(s->cfg.ingest_threads, nullptr);
     for (uint32_t k = 0; k < s->cfg.ingest_threads && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&s->s_ingest[k], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_big, cudaStreamNonBlocking);
+    s->s_big.assign(s->cfg.big_threads, nullptr);
+    for (uint32_t k = 0; k < s->cfg.big_threads && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&s->s_big[k], cudaStreamNonBlocking);
     s->s_solve.assign(s->cfg.max_inflight, nullptr);
     for (uint32_t k = 0; k < s->cfg.max_inflight && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&s->s_solve[k], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         set_error("serve_create: %s", cudaGetErrorString(e));
+        for (cudaStream_t st : s->s_ingest)
+            if (st) cudaStreamDestroy(st);
+        for (cudaStream_t st : s->s_big)
+            if (st) cudaStreamDestroy(st);
+        for (cudaStream_t st : s->s_solve)
+            if (st) cudaStreamDestroy(st);
         delete s;
         return DSG_ECUDA;
     }
     s->t0 = now_us();
     for (uint32_t k = 0; k < s->cfg.ingest_threads; ++k) s->ingesters.emplace_back(ingest_main, s, s->s_ingest[k]);
-    s->big_worker = std::thread(big_main, s);
+    for (uint32_t k = 0; k < s->cfg.big_threads; ++k) s->big_workers.emplace_back(big_main, s, s->s_big[k]);
     s->worker = std::thread(worker_main, s);
     *out = s;
     return DSG_OK;
@@ -540,6 +579,10 @@ dsg_status dsg_serve_stats(dsg_server* s, dsg_serve_info* out) {
     out->hbm_in_use = s->in_use;
     out->hbm_budget = s->cfg.hbm_budget;
     out->batches = s->batches;
+    out->big_done = s->big_done;
+    out->ingest_busy_s = s->ingest_busy_us / 1e6;
+    out->big_busy_s = s->big_busy_us / 1e6;
+    out->batch_device_s = s->batch_dev_ms / 1e3;
     out->uptime_s = (now_us() - s->t0) / 1e6;
     if (!s->lat_us.empty()) {
         std::vector<double> v = s->lat_us;
@@ -570,7 +613,8 @@ void dsg_serve_destroy(dsg_server* s) {
     s->cv_big.notify_all();
     for (auto& t : s->ingesters)
         if (t.joinable()) t.join();
-    if (s->big_worker.joinable()) s->big_worker.join();
+    for (auto& t : s->big_workers)
+        if (t.joinable()) t.join();
     for (auto& kv : s->by_ticket) {
         if (kv.second->owned) {
             free(kv.second->src);
@@ -581,7 +625,8 @@ void dsg_serve_destroy(dsg_server* s) {
     }
     for (cudaStream_t st : s->s_ingest)
         if (st) cudaStreamDestroy(st);
-    if (s->s_big) cudaStreamDestroy(s->s_big);
+    for (cudaStream_t st : s->s_big)
+        if (st) cudaStreamDestroy(st);
     for (cudaStream_t st : s->s_solve)
         if (st) cudaStreamDestroy(st);
     delete s;

@@ -36,6 +36,7 @@ Tuning current_tuning() {
         t.tail_max = env_u32("DSG_KCORE_TAIL", t.tail_max);
         t.batch_split = env_u32("DSG_BATCH_SPLIT", t.batch_split);
         t.peel_lazy = env_u32("DSG_PEEL_LAZY", t.peel_lazy) ? 1u : 0u;
+        t.peel_vec = env_u32("DSG_PEEL_VEC", t.peel_vec) ? 1u : 0u;
         if (t.tail_max > kTailMaxVertices) t.tail_max = kTailMaxVertices;
         if (t.block != 256 && t.block != 512 && t.block != 1024) t.block = 512;
         if (t.chunk_len < 32) t.chunk_len = 32;
@@ -103,6 +104,14 @@ extern "C" dsg_status dsg_set_peel_lazy(uint32_t on) {
     current_tuning();
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.peel_lazy = on ? 1u : 0u;
+    return DSG_OK;
+}
+
+extern "C" dsg_status dsg_set_peel_vec(uint32_t on) {
+    clear_error();
+    current_tuning();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.peel_vec = on ? 1u : 0u;
     return DSG_OK;
 }
 

@@ -205,6 +205,25 @@ def test_chung_lu_hubs_cross_every_row_class():
         check_peel(g, c, *pq, tag="cl15")
 
 
+@pytest.mark.parametrize("chunk_len", [32, 100, 256])
+def test_128bit_row_loads_match_the_oracle(chunk_len):
+    # long rows read as aligned 16-byte groups: chunk bounds and row starts at
+    # every residue mod 4 (masked head and tail groups), hub rows over several
+    # chunks; and a borrowed adjacency one entry past a 16-byte boundary, where
+    # the scan falls back to one entry per lane
+    raw = inputs.chung_lu(n=1 << 14, m_draws=1 << 18, gamma=2.1, mean=24.0, wmax=8000.0, seed=11)
+    c = oracle.from_raw(raw)
+    dsg.set_tuning(short_max=8, chunk_len=chunk_len, peel_vec=True)
+    g = gpu_graph(raw)
+    for pq in [(1, 1000), (1, 10), (0, 1)]:
+        check_peel(g, c, *pq, tag=f"vec chunk {chunk_len}")
+    off_d = torch.from_numpy(c.off.view(np.int64)).cuda()
+    buf = torch.zeros(c.adj.shape[0] + 4, dtype=torch.int32, device="cuda")
+    buf[1:1 + c.adj.shape[0]] = torch.from_numpy(c.adj.view(np.int32)).cuda()
+    g2 = dsg.Graph.from_csr(c.n, off_d, buf[1:1 + c.adj.shape[0]])
+    check_peel(g2, c, 1, 10, tag=f"vec misaligned chunk {chunk_len}")
+
+
 def test_star_hubs_straddle_thresholds():
     # stars whose hub degree sits at / around the tile-chunk split and chunk sizes
     pairs, base = [], 0
