@@ -328,7 +328,7 @@ typedef struct {
                                 work (2m + n of its graphs) past this, so one launch's run time, and
                                 the wait of the requests behind it, stays bounded (0: no limit) */
     uint32_t big_threads;  /* host threads solving big requests, each on its own stream with big_sms
-                              SMs (0: 1) */
+                              SMs (0: 2) */
 } dsg_serve_config;
 
 #define DSG_REQ_BORROW 0x1u   /* src/dst stay valid and unchanged until the request completes: no copy */

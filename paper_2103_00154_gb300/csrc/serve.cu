@@ -443,7 +443,7 @@ dsg_status dsg_serve_create(const dsg_serve_config* cfg, dsg_server** out) {
     if (!s->cfg.max_inflight) s->cfg.max_inflight = 4;
     if (!s->cfg.ingest_threads) s->cfg.ingest_threads = 4;
     if (!s->cfg.big_work) s->cfg.big_work = 1ull << 23;
-    if (!s->cfg.big_threads) s->cfg.big_threads = 1;
+    if (!s->cfg.big_threads) s->cfg.big_threads = 2;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess && !s->cfg.hbm_budget) {
         size_t fr = 0, tot = 0;
