@@ -429,13 +429,21 @@ __global__ void __launch_bounds__(kPartTB, 2) part_pairs_kernel(uint32_t n, uint
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         uint64_t x[kPartPer];
         uint32_t d[kPartPer], rk[kPartPer];
+        // the tile's loads first, all in flight together, then the ranking
+        uint32_t su[kPartPer / 2], sv[kPartPer / 2];
+#pragma unroll
+        for (uint32_t j = 0; j < kPartPer / 2; ++j) {
+            const uint64_t i = t * kPairs + (uint64_t)j * kPartTB + threadIdx.x;
+            su[j] = i < m_raw ? src[i] : 0u;
+            sv[j] = i < m_raw ? dst[i] : 0u;
+        }
 #pragma unroll
         for (uint32_t j = 0; j < kPartPer / 2; ++j) {
             const uint64_t i = t * kPairs + (uint64_t)j * kPartTB + threadIdx.x;
             d[2 * j] = d[2 * j + 1] = kPad;
             x[2 * j] = x[2 * j + 1] = 0;
             if (i < m_raw) {
-                const uint32_t u = src[i], v = dst[i];
+                const uint32_t u = su[j], v = sv[j];
                 // ids out of range were flagged by the histogram; the call fails after this pass
                 if (u != v && u < n && v < n) {
                     x[2 * j] = ((uint64_t)u << 32) | v;
@@ -476,13 +484,17 @@ __global__ void __launch_bounds__(kPartTB, 2) part_groups_kernel(BucketPlan pl, 
         const uint32_t nd = min(kGroupFine, F - f0);
         uint64_t x[kPartPer];
         uint32_t d[kPartPer], rk[kPartPer];
+        // the tile's loads first, all in flight together, then the ranking
+#pragma unroll
+        for (uint32_t j = 0; j < kPartPer; ++j) {
+            const uint64_t e = lo + (uint64_t)j * kPartTB + threadIdx.x;
+            x[j] = e < hi ? E1[e] : 0ull;
+        }
 #pragma unroll
         for (uint32_t j = 0; j < kPartPer; ++j) {
             const uint64_t e = lo + (uint64_t)j * kPartTB + threadIdx.x;
             d[j] = kPad;
-            x[j] = 0;
             if (e < hi) {
-                x[j] = E1[e];
                 d[j] = tab[(uint32_t)(x[j] >> 32) >> pl.rshift] - f0;
                 rk[j] = atomicAdd(&sm.cnt[d[j]], 1u);
             }
