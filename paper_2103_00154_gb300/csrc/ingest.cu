@@ -180,16 +180,28 @@ __global__ void __launch_bounds__(1024) range_hist_kernel(uint32_t n, uint64_t m
     for (uint32_t r = threadIdx.x; r < pl.nranges; r += blockDim.x) hc[r] = 0;
     __syncthreads();
     bool bad = false;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_raw;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = src[i], v = dst[i];
-        if (u >= n || v >= n) {
-            bad = true;
-            continue;
+    // four pairs per thread and step, their loads in flight together
+    constexpr uint32_t kU = 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m_raw; i0 += kU * stride) {
+        uint32_t u[kU], v[kU];
+#pragma unroll
+        for (uint32_t j = 0; j < kU; ++j) {
+            const uint64_t i = i0 + j * stride;
+            u[j] = i < m_raw ? src[i] : 0u;
+            v[j] = i < m_raw ? dst[i] : 0u;
         }
-        if (u == v) continue;
-        atomicAdd(&hc[u >> pl.rshift], 1u);
-        atomicAdd(&hc[v >> pl.rshift], 1u);
+#pragma unroll
+        for (uint32_t j = 0; j < kU; ++j) {
+            if (i0 + j * stride >= m_raw) continue;
+            if (u[j] >= n || v[j] >= n) {
+                bad = true;
+                continue;
+            }
+            if (u[j] == v[j]) continue;
+            atomicAdd(&hc[u[j] >> pl.rshift], 1u);
+            atomicAdd(&hc[v[j] >> pl.rshift], 1u);
+        }
     }
     __syncthreads();
     for (uint32_t r = threadIdx.x; r < pl.nranges; r += blockDim.x)
@@ -503,6 +515,24 @@ __global__ void __launch_bounds__(kPartTB, 2) part_groups_kernel(BucketPlan pl, 
     }
 }
 
+// Count, in cs[0, len), the entries of E2[lo, hi) whose owner (high word)
+// lies in [a, a + len); four entries per thread and step, loads first.
+__device__ __forceinline__ void count_owners(const uint64_t* __restrict__ E2, uint64_t lo, uint64_t hi, uint32_t a,
+                                             uint32_t len, uint32_t* cs) {
+    constexpr uint32_t kU = 4;
+    for (uint64_t e0 = lo + threadIdx.x; e0 < hi; e0 += kU * kRowsTB) {
+        uint32_t o[kU];
+#pragma unroll
+        for (uint32_t j = 0; j < kU; ++j) {
+            const uint64_t e = e0 + (uint64_t)j * kRowsTB;
+            o[j] = e < hi ? (uint32_t)(E2[e] >> 32) - a : 0xffffffffu;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kU; ++j)
+            if (o[j] < len) atomicAdd(&cs[o[j]], 1u);
+    }
+}
+
 // Big buckets, step 1: every kBigChunk-entry chunk counts its owners in
 // shared memory and adds the counts into cnt[] (zero beforehand).  The
 // blocks share out the row builder's items, doing those of big buckets.
@@ -526,10 +556,7 @@ __global__ void __launch_bounds__(kRowsTB) big_count_kernel(const uint32_t* __re
             const uint32_t len = min(kSpanMax, v1 - a);
             for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) cs[i] = 0;
             __syncthreads();
-            for (uint64_t e = lo + threadIdx.x; e < hi; e += kRowsTB) {
-                const uint32_t o = (uint32_t)(E2[e] >> 32) - a;
-                if (o < len) atomicAdd(&cs[o], 1u);
-            }
+            count_owners(E2, lo, hi, a, len, cs);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < len; i += kRowsTB)
                 if (cs[i]) atomicAdd(&cnt[a + i], cs[i]);
@@ -585,7 +612,7 @@ __global__ void __launch_bounds__(kRowsTB) big_starts_kernel(const PartPlan* __r
 // big bucket is one item per kBigChunk entries -- the chunk counts its
 // owners, reserves its share of each owner's row (fill[v]) and places its
 // entries there.
-__global__ void __launch_bounds__(kRowsTB) bucket_rows_kernel(const uint32_t* __restrict__ nbp,
+__global__ void __launch_bounds__(kRowsTB, 2) bucket_rows_kernel(const uint32_t* __restrict__ nbp,
                                                               const PartPlan* __restrict__ pp,
                                                               const uint32_t* __restrict__ r_pre,
                                                               const uint32_t* __restrict__ bucket_v0,
@@ -621,10 +648,7 @@ __global__ void __launch_bounds__(kRowsTB) bucket_rows_kernel(const uint32_t* __
                 const uint32_t len = min(kSpanMax, v1 - a);
                 for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) cs[i] = 0;
                 __syncthreads();
-                for (uint64_t e = lo + threadIdx.x; e < hi; e += kRowsTB) {
-                    const uint32_t o = (uint32_t)(E2[e] >> 32) - a;
-                    if (o < len) atomicAdd(&cs[o], 1u);
-                }
+                count_owners(E2, lo, hi, a, len, cs);
                 __syncthreads();
                 for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) {
                     const uint32_t c = cs[i];
@@ -646,10 +670,7 @@ __global__ void __launch_bounds__(kRowsTB) bucket_rows_kernel(const uint32_t* __
             const uint32_t len = min(kSpanMax, v1 - a);
             for (uint32_t i = threadIdx.x; i < len; i += kRowsTB) cs[i] = 0;
             __syncthreads();
-            for (uint64_t e = e0 + threadIdx.x; e < e1; e += kRowsTB) {
-                const uint32_t o = (uint32_t)(E2[e] >> 32) - a;
-                if (o < len) atomicAdd(&cs[o], 1u);
-            }
+            count_owners(E2, e0, e1, a, len, cs);
             __syncthreads();
             // exclusive scan of the counts: each thread kPer consecutive owners
             uint64_t mine = 0;
@@ -717,17 +738,31 @@ __global__ void sort_small_rows(uint32_t n, const uint64_t* __restrict__ start, 
             lists.rows[lists.base[cls] + b + __popc(same & lanemask_lt())] = (uint32_t)vl;
         }
         uint32_t small = __ballot_sync(kFullMask, vl < n && cls < 0);
-        while (small) {
-            uint32_t src_lane = __ffs(small) - 1;
+        // the row starts of the group's small rows in one load; each row's
+        // entries are loaded while the row before it is sorted
+        const uint64_t mystart = (vl < n && cls < 0 && mylen) ? start[vl] : 0;
+        uint32_t nx_len = 0, nx_lane = 0, nx_x = kPad;
+        uint64_t nx_b = 0;
+        auto fetch = [&]() {
+            nx_lane = __ffs(small) - 1;
             small &= small - 1;
-            uint64_t v = v0 + src_lane;
-            uint32_t len = __shfl_sync(kFullMask, mylen, src_lane);
+            nx_len = __shfl_sync(kFullMask, mylen, nx_lane);
+            nx_b = __shfl_sync(kFullMask, mystart, nx_lane);
+            nx_x = lane < nx_len ? tmp[nx_b + lane] : kPad;
+        };
+        bool have = small != 0;
+        if (have) fetch();
+        while (have) {
+            const uint64_t v = v0 + nx_lane;
+            const uint32_t len = nx_len;
+            const uint64_t b = nx_b;
+            uint32_t x = nx_x;
+            have = small != 0;
+            if (have) fetch();
             if (len == 0) {
                 if (lane == 0) newlen[v] = 0;
                 continue;
             }
-            uint64_t b = start[v];
-            uint32_t x = lane < len ? tmp[b + lane] : kPad;
 #pragma unroll
             for (uint32_t k = 2; k <= 32; k <<= 1) {
 #pragma unroll
