@@ -715,8 +715,52 @@ struct ClassLists {
     uint32_t base[kClasses];    // start of each class in rows
 };
 
-// Rows of <= 32 entries: one warp per row, one value per lane, bitonic
-// network over shuffles, dedup by comparing with the previous lane.  Longer
+// Rows of <= 32 entries, 32 / W rows at a time per warp: row s of a batch in
+// lanes [sW, sW + W), one value per lane, a bitonic network over shuffles
+// within the segment (ascending in every segment), dedup by comparing with
+// the previous lane of the segment.  W = 8, 16 or 32 by the rows' lengths.
+// `mask`: the group's rows (lane = row v0 + lane) still to do in this width.
+template <uint32_t W>
+__device__ __forceinline__ void sort_small_batches(uint32_t mask, uint64_t v0, uint32_t mylen, uint64_t mystart,
+                                                   uint32_t* __restrict__ tmp, uint32_t* __restrict__ newlen,
+                                                   uint32_t lane) {
+    constexpr uint32_t R = 32 / W;
+    const uint32_t seg = lane / W, p = lane % W;
+    const uint32_t segmask = (W == 32 ? 0xffffffffu : ((1u << W) - 1u)) << (seg * W);
+    while (mask) {
+        uint32_t src = 32;  // this segment's row (lane of the group), 32: none
+#pragma unroll
+        for (uint32_t r = 0; r < R; ++r) {
+            if (mask) {
+                const uint32_t l = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (seg == r) src = l;
+            }
+        }
+        const uint32_t len = __shfl_sync(kFullMask, mylen, src & 31u);
+        const uint64_t b = __shfl_sync(kFullMask, mystart, src & 31u);
+        uint32_t x = (src < 32 && p < len) ? tmp[b + p] : kPad;
+#pragma unroll
+        for (uint32_t k = 2; k <= W; k <<= 1) {
+#pragma unroll
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                const uint32_t y = __shfl_xor_sync(kFullMask, x, j);
+                const bool up = k == W || (lane & k) == 0;
+                const bool lower = (lane & j) == 0;
+                // lower lane keeps min when ascending, max when descending
+                x = (lower == up) ? min(x, y) : max(x, y);
+            }
+        }
+        const uint32_t prev = __shfl_up_sync(kFullMask, x, 1);
+        const bool keep = x != kPad && (p == 0 || x != prev);
+        const uint32_t bal = __ballot_sync(kFullMask, keep) & segmask;
+        if (keep) tmp[b + __popc(bal & lanemask_lt())] = x;
+        if (p == 0 && src < 32) newlen[v0 + src] = __popc(bal);
+    }
+}
+
+// Rows of <= 32 entries are sorted and deduplicated in place by
+// sort_small_batches (a warp takes 32 consecutive rows at a time); longer
 // rows are appended to their class list (warp-aggregated per class).
 __global__ void sort_small_rows(uint32_t n, const uint64_t* __restrict__ start, const uint32_t* __restrict__ cnt,
                                 uint32_t* __restrict__ tmp, uint32_t* __restrict__ newlen, ClassLists lists,
@@ -724,7 +768,6 @@ __global__ void sort_small_rows(uint32_t n, const uint64_t* __restrict__ start, 
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    // one warp walks 32 rows at a time for the class append, then sorts its small rows
     for (uint64_t v0 = gw * 32; v0 < n; v0 += nw * 32) {
         uint64_t vl = v0 + lane;
         uint32_t mylen = vl < n ? cnt[vl] : 0;
@@ -737,49 +780,15 @@ __global__ void sort_small_rows(uint32_t n, const uint64_t* __restrict__ start, 
             b = __shfl_sync(same, b, leader);
             lists.rows[lists.base[cls] + b + __popc(same & lanemask_lt())] = (uint32_t)vl;
         }
-        uint32_t small = __ballot_sync(kFullMask, vl < n && cls < 0);
-        // the row starts of the group's small rows in one load; each row's
-        // entries are loaded while the row before it is sorted
-        const uint64_t mystart = (vl < n && cls < 0 && mylen) ? start[vl] : 0;
-        uint32_t nx_len = 0, nx_lane = 0, nx_x = kPad;
-        uint64_t nx_b = 0;
-        auto fetch = [&]() {
-            nx_lane = __ffs(small) - 1;
-            small &= small - 1;
-            nx_len = __shfl_sync(kFullMask, mylen, nx_lane);
-            nx_b = __shfl_sync(kFullMask, mystart, nx_lane);
-            nx_x = lane < nx_len ? tmp[nx_b + lane] : kPad;
-        };
-        bool have = small != 0;
-        if (have) fetch();
-        while (have) {
-            const uint64_t v = v0 + nx_lane;
-            const uint32_t len = nx_len;
-            const uint64_t b = nx_b;
-            uint32_t x = nx_x;
-            have = small != 0;
-            if (have) fetch();
-            if (len == 0) {
-                if (lane == 0) newlen[v] = 0;
-                continue;
-            }
-#pragma unroll
-            for (uint32_t k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                    uint32_t y = __shfl_xor_sync(kFullMask, x, j);
-                    bool up = (lane & k) == 0;
-                    bool lower = (lane & j) == 0;
-                    // lower lane keeps min when ascending, max when descending
-                    x = (lower == up) ? min(x, y) : max(x, y);
-                }
-            }
-            uint32_t prev = __shfl_up_sync(kFullMask, x, 1);
-            bool keep = x != kPad && (lane == 0 || x != prev);
-            uint32_t bal = __ballot_sync(kFullMask, keep);
-            if (keep) tmp[b + __popc(bal & lanemask_lt())] = x;
-            if (lane == 0) newlen[v] = __popc(bal);
-        }
+        const bool small = vl < n && cls < 0;
+        if (small && mylen == 0) newlen[vl] = 0;
+        const uint64_t mystart = (small && mylen) ? start[vl] : 0;
+        sort_small_batches<8>(__ballot_sync(kFullMask, small && mylen && mylen <= 8), v0, mylen, mystart, tmp,
+                              newlen, lane);
+        sort_small_batches<16>(__ballot_sync(kFullMask, small && mylen > 8 && mylen <= 16), v0, mylen, mystart,
+                               tmp, newlen, lane);
+        sort_small_batches<32>(__ballot_sync(kFullMask, small && mylen > 16), v0, mylen, mystart, tmp, newlen,
+                               lane);
     }
 }
 
