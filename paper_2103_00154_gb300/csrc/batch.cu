@@ -301,6 +301,14 @@ static cudaError_t to_device(Scratch& sc, const T* src, size_t count, cudaStream
     return e;
 }
 
+// ends[g] = off[vb[g]] for g = 0..G: every graph's first adjacency offset
+// (and the batch's end), gathered for one copy to the host.
+__global__ void gather_ends_kernel(const uint64_t* __restrict__ off, const uint64_t* __restrict__ vb, uint32_t G1,
+                                   uint64_t* __restrict__ ends) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < G1) ends[g] = off[vb[g]];
+}
+
 }  // namespace dsg
 
 using namespace dsg;
@@ -330,22 +338,32 @@ extern "C" dsg_status dsg_batch_solve(const dsg_batch* b, dsg_batch_result* r, v
     DSG_TRY_CUDA(copy_any(&total, b->off + N, sizeof(uint64_t), s));
     DSG_TRY_CUDA(cudaStreamSynchronize(s));
     DSG_CHECK_ARG(total == 0 || b->adj, "adj is NULL");
-    // largest first (by adjacency length, then vertices)
+    Scratch sc(s);
+    const uint64_t* d_off;
+    DSG_TRY_CUDA(to_device(sc, b->off, N + 1, s, &d_off));
+    // largest first (by adjacency length, then vertices): every graph's first offset, gathered
+    // on the device and copied in one piece
     std::vector<uint64_t> hoff_ends(G + 1);
-    for (uint32_t g = 0; g <= G; ++g) {
-        DSG_TRY_CUDA(copy_any(&hoff_ends[g], b->off + vb[g], sizeof(uint64_t), s));
+    {
+        const uint64_t* d_vb;
+        DSG_TRY_CUDA(to_device(sc, vb.data(), G + 1, s, &d_vb));
+        uint64_t* d_ends;
+        DSG_TRY_CUDA(sc.get(&d_ends, G + 1));
+        {
+            LaunchScope ls("batch_ends", s);
+            gather_ends_kernel<<<(G + 1 + 255) / 256, 256, 0, s>>>(d_off, d_vb, G + 1, d_ends);
+        }
+        DSG_TRY_CUDA(cudaGetLastError());
+        DSG_TRY_CUDA(cudaMemcpyAsync(hoff_ends.data(), d_ends, (G + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        DSG_TRY_CUDA(cudaStreamSynchronize(s));
     }
-    DSG_TRY_CUDA(cudaStreamSynchronize(s));
     std::vector<uint32_t> order(G);
     for (uint32_t g = 0; g < G; ++g) order[g] = g;
     auto work = [&](uint32_t x) { return (hoff_ends[x + 1] - hoff_ends[x]) + (vb[x + 1] - vb[x]); };
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return work(x) > work(y); });
-    Scratch sc(s);
     BatchArgs a;
     a.G = G;
-    const uint64_t* d_off;
     const uint32_t* d_adj;
-    DSG_TRY_CUDA(to_device(sc, b->off, N + 1, s, &d_off));
     DSG_TRY_CUDA(to_device(sc, b->adj, total, s, &d_adj));
     DSG_TRY_CUDA(to_device(sc, b->eps_num, G, s, &a.p));
     DSG_TRY_CUDA(to_device(sc, b->eps_den, G, s, &a.q));
