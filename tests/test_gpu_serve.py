@@ -59,6 +59,40 @@ def test_requests_match_the_oracle():
         assert st["hbm_in_use"] == 0
 
 
+@pytest.mark.parametrize("big_threads,big_work,batch_work,inflight",
+                         [(3, 20000, 0, 2), (1, 1, 0, 4), (2, 0, 50000, 8), (2, 2 ** 64 - 1, 1, 1)])
+def test_server_settings_do_not_change_results(big_threads, big_work, batch_work, inflight):
+    # requests solved alone by several big-request threads (big_work 1: every
+    # one), launches closed by a work cap (1: one graph per launch), many or
+    # one launch in flight, no big-request path at all: every result is the
+    # oracle's and the time split adds up
+    pool = _pool(k=12, seed=5)
+    csrs = [oracle.from_raw(g) for g in pool]
+    rng = np.random.default_rng(2)
+    with dsg.Server(max_batch=8, big_threads=big_threads, big_work=big_work, max_batch_work=batch_work,
+                    max_inflight=inflight) as srv:
+        tickets = []
+        for i in range(30):
+            j = int(rng.integers(len(pool)))
+            p, q = [(1, 100), (1, 10)][i % 2]
+            want_core = i % 3 == 0
+            out_set = np.zeros(max(pool[j].n, 1), np.uint8)
+            core = np.zeros(max(pool[j].n, 1), np.uint32) if want_core else None
+            t = srv.submit(pool[j].n, pool[j].src, pool[j].dst, p, q, want_core, out_set, core)
+            assert t is not None
+            tickets.append((t, j, p, q, out_set, core))
+        for t, j, p, q, out_set, core in tickets:
+            _check(srv.wait(t), csrs[j], p, q, out_set, core)
+        st = srv.stats()
+        assert st["completed"] == 30
+        if big_work == 1:
+            assert st["big_done"] == 30
+        if big_work == 2 ** 64 - 1:
+            assert st["big_done"] == 0
+        assert st["ingest_busy_s"] > 0
+        assert st["big_busy_s"] >= 0 and st["batch_device_s"] >= 0
+
+
 def test_same_result_alone_and_in_the_mix():
     pool = _pool(k=16, seed=9)
     probe = inputs.batch_graph(3, n_lo=20000, n_hi=60000, threads=1)
