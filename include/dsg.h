@@ -411,7 +411,7 @@ dsg_status dsg_set_local_max(uint32_t local_max, uint32_t local_work);
 /* Core numbers: a vertex whose row has at most inline_max entries and that a
  * block's level scan claims is drained by that block; longer rows go to the
  * level-wide queue in pieces of at most chunk_len entries, which every block
- * takes from.  Default 4096; DSG_INLINE_MAX.  Results never depend on it. */
+ * takes from.  Default 256; DSG_INLINE_MAX.  Results never depend on it. */
 dsg_status dsg_set_inline_max(uint32_t inline_max);
 /* Core numbers: once at most max_vertices vertices remain after a level, the
  * remaining graph is compacted (rows cut to the remaining neighbours, which

@@ -32,7 +32,7 @@ def round_bound(n: int, p: int, q: int) -> int:
 
 
 def set_tuning(block: int = 512, blocks_per_sm: int = 0, short_max: int = 32, chunk_len: int = 256,
-               hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384, inline_max: int = 4096,
+               hot_deg: int = 0, local_max: int = 1024, local_work: int = 16384, inline_max: int = 256,
                kcore_tail: int = 65536, batch_split: int = 0, peel_lazy: bool = True, peel_vec: bool = False):
     N.check(lib().dsg_set_tuning(block, blocks_per_sm, short_max, chunk_len), "set_tuning")
     N.check(lib().dsg_set_hot_degree(hot_deg), "set_hot_degree")

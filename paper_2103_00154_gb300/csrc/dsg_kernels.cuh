@@ -25,7 +25,7 @@ struct Tuning {
                                 // several times by every block)
     uint32_t local_max = 1024;  // k-core: rows up to this length reached while draining stay in the block
     uint32_t local_work = 16384; // k-core: ... while that block's local share of the sub-round stays within this
-    uint32_t inline_max = 4096;  // k-core: rows up to this length claimed by a block's level scan are drained by
+    uint32_t inline_max = 256;   // k-core: rows up to this length claimed by a block's level scan are drained by
                                  // that block; longer ones by every warp in the next sub-round
     uint32_t tail_max = 65536;   // k-core: once at most this many vertices remain, one thread-block cluster
                                  // finishes the levels on the compacted remaining graph (0: never)
