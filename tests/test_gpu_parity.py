@@ -190,6 +190,31 @@ def test_ingest_row_classes_at_scale():
     assert deg.max() > 8192
 
 
+def test_small_rows_at_segment_boundaries():
+    # rows of 1..40 distinct neighbours, each pair given up to three times in
+    # both directions: the small-row sort's 8-, 16- and 32-entry segments
+    # (four, two and one row per warp) and the warp rows just above them,
+    # with duplicates to drop at every length; the rows of one 32-row group
+    # mix all lengths
+    rng = np.random.default_rng(41)
+    n = 4096
+    pairs = []
+    for v in range(1024):
+        d = 1 + (v * 7) % 40
+        nb = rng.choice(np.arange(1024, n), size=d, replace=False)
+        for u in nb:
+            for _ in range(int(rng.integers(1, 4))):
+                pairs.append((v, int(u)) if rng.integers(2) else (int(u), v))
+    raw = inputs.from_pairs(n, pairs, "segment-boundaries")
+    c = oracle.from_raw(raw)
+    deg = np.diff(c.off.astype(np.int64))
+    assert {8, 9, 16, 17, 32, 33} <= set(deg[:1024].tolist())
+    g = gpu_graph(raw)
+    check_csr(g, c, raw.name)
+    check_core(g, c, raw.name)
+    check_peel(g, c, 1, 10, raw.name)
+
+
 def test_chung_lu_hubs_cross_every_row_class():
     # hubs of expected degree up to 30000: rows pass 32 (tile/chunk split,
     # warp/block ingest), 256 (several chunks), 4096 and 8192 (merge-path
